@@ -1,0 +1,180 @@
+/*
+ * pai.h -- C ABI of the GB300 (sm_103a) photoacoustic Fourier reconstruction
+ * library (libpai.so).
+ *
+ * Method: Haltmeier, Scherzer, Zangerl, "A Reconstruction Algorithm for
+ * Photoacoustic Imaging based on the Nonuniform FFT", Algorithm 2
+ * ("FouRecNufft"), generalised from the paper's 2-D unit grid to line (d = 2)
+ * and planar (d = 3) detectors on arbitrary rectangular grids:
+ *
+ *   1. lateral FFT of the detector data over the detector coordinate(s)
+ *      (Eq. fft-1a);
+ *   2. for every lateral frequency K_lat a 1-D nonuniform FFT along time
+ *      (Algorithm 1: Kaiser-Bessel prescale, zero padding to the oversampled
+ *      length c*nt, FFT, truncated window-weighted gather) evaluating the
+ *      temporal spectrum at the nodes omega = c_s * sign(Kz) * |K|
+ *      (Eq. fft-2, Eq. dft-2d);
+ *   3. the weight of the exact inversion formula, 2|Kz|/|K| times
+ *      c_s*dt/dz (Eq. fft-0, Eq. inv);
+ *   4. the inverse FFT to the image, real part (Eq. fft-1).
+ *
+ * Grids.  Detector data p[x][y][n] = p(x*dx, y*dy, n*dt), n = 0..nt-1, t = 0
+ * at the illumination.  Image f[x][y][q] ~ f(x*dx, y*dy, q*dz), q = 0..nz-1,
+ * depth 0 = detector plane.  In 2-D drop the y index (ny = 1).  Both arrays
+ * are FP32, contiguous, last index fastest.
+ *
+ * Memory.  Every pointer passed to pai_reconstruct / pai_adjoint is a DEVICE
+ * pointer on the plan's device, owned by the caller, not retained after the
+ * call.  Every pointer passed to pai_reconstruct_host is a HOST pointer.  The
+ * plan owns its workspace, its cuFFT plans and its CUDA graphs.
+ *
+ * Streams.  All calls except pai_plan*, pai_destroy and pai_reconstruct_host
+ * are asynchronous on the plan's stream (set at plan time, changeable with
+ * pai_set_stream).  A plan must not be used by two host threads at once.
+ *
+ * Errors.  Every function returns a pai_status; nothing else crosses the ABI.
+ * On failure, out-parameters are left untouched and no work is enqueued.
+ */
+#ifndef PAI_H
+#define PAI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pai_plan_s* pai_plan_t;
+
+typedef enum {
+  PAI_OK = 0,
+  PAI_ERR_INVALID_ARG = 1,  /* bad geometry, size or pointer                 */
+  PAI_ERR_UNSUPPORTED = 2,  /* valid but outside what this build implements  */
+  PAI_ERR_OOM = 3,          /* device or host allocation failed              */
+  PAI_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed   */
+  PAI_ERR_CUFFT = 5,        /* a cuFFT call failed                           */
+  PAI_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up            */
+} pai_status;
+
+/* Problem statement (paper Sec. 2 and Sec. 4, Eq. gd / Eq. fd).
+ * Parameters of the nonuniform FFT (Algorithm 1): 0 selects the default.   */
+typedef struct {
+  int dim;              /* 2 = line detector, 3 = planar detector             */
+  int nx, ny;           /* detector grid = lateral image grid; ny = 1 in 2-D   */
+  double dx, dy;        /* detector spacings (> 0)                            */
+  int nt;               /* time samples (even, >= 2)                          */
+  double dt;            /* time step (> 0)                                    */
+  double c;             /* speed of sound (> 0)                               */
+  int nz;               /* image depth samples (even, >= 2)                   */
+  double dz;            /* depth spacing (> 0)                                */
+  double oversampling;  /* NUFFT oversampling c_os > 1; 0 -> 2.  The padded
+                           temporal FFT length is the smallest power of two
+                           >= c_os*nt, so the effective c_os may be larger.  */
+  double K;             /* interpolation length K (> 0); 0 -> chosen so the
+                           window's truncation error is <= 1e-8.  The number of
+                           taps per node is 2*ceil(c_os*K) and stays fixed when
+                           the effective oversampling grows.                  */
+  double alpha;         /* Kaiser-Bessel shape; 0 -> pi*(2c_os - 1)*(1 - 1e-3),
+                           must be < pi*(2c_os - 1) (Lemma on Fourmont's
+                           identity).                                        */
+} pai_geometry;
+
+/* Read-only description of a plan (for reports and tests). */
+typedef struct {
+  int count;              /* problems in the plan (1 unless batched)            */
+  int M;                  /* padded temporal FFT length of problem 0            */
+  int taps;               /* taps per node (2*ceil(c_os*K))                      */
+  double oversampling;    /* effective c_os = M/nt of problem 0                  */
+  double K, alpha;        /* effective window parameters of problem 0           */
+  double predicted_error; /* FP64 truncation error of the window identity (max
+                             over the batch), see pai_plan                       */
+  int threads_per_cta;    /* row-kernel CTA size chosen by the tuner             */
+  int ctas;               /* row-kernel grid size (persistent CTAs)              */
+  int rows;               /* lateral-frequency rows processed per call          */
+  long long nodes;        /* nodes evaluated per call (sum over the batch)      */
+  size_t workspace_bytes; /* device bytes owned by the plan                     */
+  int uses_graph;         /* 1 if calls replay a captured CUDA graph            */
+} pai_plan_info;
+
+/* Create a plan for one reconstruction problem (Algorithm 2).
+ * g:           problem statement; read during the call only.
+ * cuda_stream: cudaStream_t (may be NULL = legacy default stream) on the
+ *              current device; all later work of the plan is enqueued there.
+ * out:         receives the plan on success.
+ * Synchronises the device.  Validation (PAI_ERR_INVALID_ARG): dim in {2,3};
+ * nx, nz, nt even and >= 2 (ny even and >= 2 in 3-D); spacings, dt and c > 0;
+ * oversampling == 0 or > 1; K >= 0; 0 <= alpha < pi*(2 c_os_eff - 1).        */
+pai_status pai_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out);
+
+/* Create one plan for `count` independent 2-D or 3-D problems (g[0..count-1])
+ * executed together: one lateral FFT per problem, ONE persistent row-kernel
+ * launch over every lateral-frequency row of every problem, one inverse FFT
+ * per problem, all replayed as one CUDA graph.  The problems share the tap
+ * count (the largest over the batch); each keeps its own oversampling.
+ * Data and images of the batch are concatenated in g-order.                  */
+pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream, pai_plan_t* out);
+
+/* Reconstruction f = R p (Algorithm 2).
+ * d_p: device, FP32, sum over problems of nx*ny*nt values, read only.
+ * d_f: device, FP32, sum over problems of nx*ny*nz values, overwritten.
+ * Asynchronous on the plan's stream.                                         */
+pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f);
+
+/* Adjoint p_bar = R^T h of the operator pai_reconstruct applies (the exact
+ * transpose of the discretised Algorithm 2 under real inner products:
+ * forward image FFT, window spread from the nodes onto the oversampled grid
+ * in gather form, inverse oversampled FFT, prescale, inverse lateral FFT).
+ * d_h: device, FP32, image-shaped, read only.  d_pbar: device, FP32,
+ * data-shaped, overwritten.  Asynchronous on the plan's stream.              */
+pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar);
+
+/* The image spectrum before the inverse FFT: steps 1-3 of Algorithm 2.
+ * d_fhat: device, interleaved complex64, [nx][ny][nz/2+1] per problem
+ * (half spectrum in depth, full lateral spectrum), including the factor
+ * 1/(nx*ny*nz) of the inverse FFT.  Entry l = nz/2 holds the mean of the two
+ * Nyquist nodes (the real part of the inverse DFT depends only on it).        */
+pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat);
+
+/* End-to-end reconstruction from HOST memory: copies h_p to the device,
+ * runs pai_reconstruct and copies the image back into h_f, then synchronises
+ * the plan's stream.  h_p / h_f: host FP32 arrays sized as for
+ * pai_reconstruct (page-locked memory gives full copy speed).  Uses
+ * plan-owned device staging buffers allocated on first use.                  */
+pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f);
+
+/* Change the stream later calls are enqueued on (cudaStream_t or NULL).     */
+pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream);
+
+/* Fill *info with the plan's parameters.                                     */
+pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info);
+
+/* Cumulative count of kernels and cuFFT executions this plan has enqueued
+ * (graph replays count the kernels inside the graph).                        */
+pai_status pai_launch_count(pai_plan_t plan, long long* kernels);
+
+/* Release the plan and everything it owns.  Synchronises the plan's stream.
+ * NULL is accepted and ignored.                                              */
+pai_status pai_destroy(pai_plan_t plan);
+
+/* Host-only probe of the plan-time window math (no GPU needed).  For half
+ * tap count H = c*K, shape beta = alpha/c and oversampling c it writes
+ * phi_out[i] = psi_hat(y_i / c) / psi_hat(0) for the n grid offsets y[i]
+ * (the Kaiser-Bessel transform of Sec. 3.2 in grid units, analytic
+ * continuation beyond |y| = H), and *pred_err = the largest error of
+ * Fourmont's identity (Lemma in Sec. 3.1) truncated to the 2H taps, over
+ * theta in [-pi, pi] and all node offsets, and *fit_err = the largest error
+ * of the FP32 tap polynomials the kernels use, relative to psi_hat(0).
+ * Any output pointer may be NULL.  Returns PAI_ERR_INVALID_ARG unless
+ * 2 <= H <= 12, c > 1 and pi < beta*c <= pi*(2c - 1) (the paper's own example
+ * alpha = 3 pi at c = 2 sits on that boundary).                              */
+pai_status pai_window_probe(int H, double beta, double c, int n, const double* y, double* phi_out,
+                            double* pred_err, double* fit_err);
+
+/* Static description of a status code; never NULL.                           */
+const char* pai_status_string(pai_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAI_H */

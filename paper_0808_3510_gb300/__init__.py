@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) NUFFT-based Fourier reconstruction for planar and line-detector
+photoacoustic imaging (Haltmeier, Scherzer, Zangerl; Algorithm 2).
+
+This module is the thin Python binding of ``libpai.so`` (C ABI in
+``include/pai.h``): it marshals torch tensors into device pointers and the
+current CUDA stream.  Every step of the reconstruction runs in the library's
+CUDA kernels and cuFFT; there is no CPU or PyTorch fallback.  If the library
+has not been built, every entry point raises.
+
+Quick use::
+
+    import torch, paper_0808_3510_gb300 as pai
+    plan = pai.Plan(dict(dim=2, nx=128, nt=256, nz=128, dx=1, dt=1, c=1, dz=1))
+    f = plan.reconstruct(p_cuda_float32)          # [nx][nz]
+    f = pai.PAIRecon.apply(p, plan)                # differentiable in p
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, List, Optional, Sequence
+
+import torch
+
+__all__ = ["Plan", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "library_path", "load_library", "geometry",
+           "window_probe"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libpai.so")
+_lock = threading.Lock()
+_lib = None
+
+PAI_OK = 0
+_STATUS = {
+    0: "success", 1: "invalid argument", 2: "unsupported configuration", 3: "out of memory",
+    4: "CUDA error", 5: "cuFFT error", 6: "device wait timed out",
+}
+
+
+class PAIError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(status, 'unknown status')} (pai_status {status})")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    """Mirror of ``pai_geometry``."""
+
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("nt", ctypes.c_int), ("dt", ctypes.c_double), ("c", ctypes.c_double),
+        ("nz", ctypes.c_int), ("dz", ctypes.c_double),
+        ("oversampling", ctypes.c_double), ("K", ctypes.c_double), ("alpha", ctypes.c_double),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    """Mirror of ``pai_plan_info``."""
+
+    _fields_ = [
+        ("count", ctypes.c_int), ("M", ctypes.c_int), ("taps", ctypes.c_int),
+        ("oversampling", ctypes.c_double), ("K", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("predicted_error", ctypes.c_double), ("threads_per_cta", ctypes.c_int), ("ctas", ctypes.c_int),
+        ("rows", ctypes.c_int), ("nodes", ctypes.c_longlong), ("workspace_bytes", ctypes.c_size_t),
+        ("uses_graph", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libpai.so (built by ``paper_0808_3510_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"libpai.so not found at {_LIB_PATH}; build it with `python -m paper_0808_3510_gb300.build` "
+                "(the reconstruction has no CPU fallback)")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, fp = ctypes.c_void_p, ctypes.c_void_p
+        st = ctypes.c_int
+        G = ctypes.POINTER(Geometry)
+        lib.pai_plan.argtypes = [G, vp, ctypes.POINTER(vp)]
+        lib.pai_plan.restype = st
+        lib.pai_plan_batched.argtypes = [G, ctypes.c_int, vp, ctypes.POINTER(vp)]
+        lib.pai_plan_batched.restype = st
+        for name in ("pai_reconstruct", "pai_adjoint", "pai_spectrum", "pai_reconstruct_host"):
+            getattr(lib, name).argtypes = [vp, fp, fp]
+            getattr(lib, name).restype = st
+        lib.pai_set_stream.argtypes = [vp, vp]
+        lib.pai_set_stream.restype = st
+        lib.pai_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        lib.pai_get_info.restype = st
+        lib.pai_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        lib.pai_launch_count.restype = st
+        lib.pai_destroy.argtypes = [vp]
+        lib.pai_destroy.restype = st
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.pai_window_probe.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp,
+                                         dp]
+        lib.pai_window_probe.restype = st
+        lib.pai_status_string.argtypes = [st]
+        lib.pai_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != PAI_OK:
+        raise PAIError(status, where)
+
+
+def geometry(g) -> Geometry:
+    """Build a ``pai_geometry`` from a dict or an object with the same field names
+    (dim, nx, ny, dx, dy, nt, dt, c, nz, dz; optional oversampling, K, alpha)."""
+    get = (lambda k, d=None: g.get(k, d)) if isinstance(g, dict) else (lambda k, d=None: getattr(g, k, d))
+    dim = int(get("dim"))
+    return Geometry(
+        dim, int(get("nx")), int(get("ny", 1) or 1) if dim == 3 else 1,
+        float(get("dx", 1.0)), float(get("dy", 1.0) or 1.0) if dim == 3 else 1.0,
+        int(get("nt")), float(get("dt", 1.0)), float(get("c", 1.0)),
+        int(get("nz")), float(get("dz", 1.0)),
+        float(get("oversampling", 0.0) or 0.0), float(get("K", 0.0) or 0.0), float(get("alpha", 0.0) or 0.0),
+    )
+
+
+def _numel(g: Geometry, last: int) -> int:
+    return g.nx * (g.ny if g.dim == 3 else 1) * last
+
+
+def _shape(g: Geometry, last: int):
+    return (g.nx, last) if g.dim == 2 else (g.nx, g.ny, last)
+
+
+def window_probe(H: int, beta: float, c: float, y=()):
+    """Plan-time window math (host only): returns (phi(y)/phi(0) list, predicted
+    truncation error, FP32 tap-polynomial fit error).  See ``pai_window_probe``."""
+    lib = load_library()
+    n = len(y)
+    ya = (ctypes.c_double * max(n, 1))(*y)
+    out = (ctypes.c_double * max(n, 1))()
+    pe, fe = ctypes.c_double(), ctypes.c_double()
+    _check(lib.pai_window_probe(H, beta, c, n, ya, out, ctypes.byref(pe), ctypes.byref(fe)), "pai_window_probe")
+    return [out[i] for i in range(n)], pe.value, fe.value
+
+
+class Plan:
+    """A reconstruction plan: one problem, or a batch of independent problems.
+
+    ``Plan(g)`` wraps ``pai_plan``; ``Plan([g0, g1, ...])`` wraps
+    ``pai_plan_batched`` (inputs and outputs are then flat concatenations).
+    The plan lives on the current CUDA device; calls run on torch's current
+    stream.
+    """
+
+    def __init__(self, geoms, stream: Optional[torch.cuda.Stream] = None, overrides: Optional[dict] = None):
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_0808_3510_gb300 needs a CUDA device")
+        single = not isinstance(geoms, (list, tuple))
+        items = [geoms] if single else list(geoms)
+        gs = []
+        for g in items:
+            gg = geometry(g)
+            if overrides:
+                for k, v in overrides.items():
+                    setattr(gg, k, v)
+            gs.append(gg)
+        self.geoms: List[Geometry] = gs
+        self.batched = not single
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = s.cuda_stream
+        arr = (Geometry * len(gs))(*gs)
+        h = ctypes.c_void_p()
+        if single:
+            _check(lib.pai_plan(arr, ctypes.c_void_p(self._stream), ctypes.byref(h)), "pai_plan")
+        else:
+            _check(lib.pai_plan_batched(arr, len(gs), ctypes.c_void_p(self._stream), ctypes.byref(h)),
+                   "pai_plan_batched")
+        self._h = h
+        self._lib = lib
+        self.data_numel = sum(_numel(g, g.nt) for g in gs)
+        self.image_numel = sum(_numel(g, g.nz) for g in gs)
+        self.spectrum_numel = sum(_numel(g, g.nz // 2 + 1) for g in gs)
+
+    # -- helpers ---------------------------------------------------------
+    def _sync_stream(self):
+        cur = torch.cuda.current_stream(self.device).cuda_stream
+        if cur != self._stream:
+            _check(self._lib.pai_set_stream(self._h, ctypes.c_void_p(cur)), "pai_set_stream")
+            self._stream = cur
+
+    def _check_in(self, t: torch.Tensor, numel: int, what: str):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float32:
+            raise ValueError(f"{what} must be a float32 tensor on {self.device}")
+        if not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{what} must be contiguous with {numel} elements (got {tuple(t.shape)})")
+
+    def _out_shape(self, last_attr: str):
+        if self.batched:
+            return (self.image_numel if last_attr == "nz" else self.data_numel,)
+        g = self.geoms[0]
+        return _shape(g, getattr(g, last_attr))
+
+    # -- operators ---------------------------------------------------------
+    def reconstruct(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """f = R p (Algorithm 2).  p: [nx][(ny)][nt] float32 on the plan's device."""
+        self._check_in(p, self.data_numel, "p")
+        if out is None:
+            out = torch.empty(self._out_shape("nz"), device=self.device, dtype=torch.float32)
+        self._check_in(out, self.image_numel, "out")
+        self._sync_stream()
+        _check(self._lib.pai_reconstruct(self._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+               "pai_reconstruct")
+        return out
+
+    def adjoint(self, h: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """p_bar = R^T h, the exact transpose of :meth:`reconstruct`."""
+        self._check_in(h, self.image_numel, "h")
+        if out is None:
+            out = torch.empty(self._out_shape("nt"), device=self.device, dtype=torch.float32)
+        self._check_in(out, self.data_numel, "out")
+        self._sync_stream()
+        _check(self._lib.pai_adjoint(self._h, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+               "pai_adjoint")
+        return out
+
+    def spectrum(self, p: torch.Tensor) -> torch.Tensor:
+        """Half image spectrum (steps 1-3), complex64 [nx][(ny)][nz/2+1] (flat when batched)."""
+        self._check_in(p, self.data_numel, "p")
+        out = torch.empty(self.spectrum_numel * 2, device=self.device, dtype=torch.float32)
+        self._sync_stream()
+        _check(self._lib.pai_spectrum(self._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+               "pai_spectrum")
+        c = torch.view_as_complex(out.view(-1, 2))
+        if not self.batched:
+            g = self.geoms[0]
+            c = c.view(_shape(g, g.nz // 2 + 1))
+        return c
+
+    def reconstruct_host(self, p_host: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """End to end from host memory (pai_reconstruct_host): copies in, reconstructs, copies out."""
+        if p_host.device.type != "cpu" or p_host.dtype != torch.float32 or not p_host.is_contiguous():
+            raise ValueError("p_host must be a contiguous float32 CPU tensor")
+        if p_host.numel() != self.data_numel:
+            raise ValueError("p_host has the wrong number of elements")
+        if out is None:
+            out = torch.empty(self._out_shape("nz"), dtype=torch.float32, pin_memory=p_host.is_pinned())
+        self._sync_stream()
+        _check(self._lib.pai_reconstruct_host(self._h, ctypes.c_void_p(p_host.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr())), "pai_reconstruct_host")
+        return out
+
+    # -- introspection ------------------------------------------------------
+    @property
+    def info(self) -> dict:
+        i = PlanInfo()
+        _check(self._lib.pai_get_info(self._h, ctypes.byref(i)), "pai_get_info")
+        return i.as_dict()
+
+    @property
+    def kernel_launches(self) -> int:
+        n = ctypes.c_longlong()
+        _check(self._lib.pai_launch_count(self._h, ctypes.byref(n)), "pai_launch_count")
+        return int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pai_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PAIRecon(torch.autograd.Function):
+    """Differentiable reconstruction: forward = :meth:`Plan.reconstruct`,
+    backward = :meth:`Plan.adjoint` (the operator is linear)."""
+
+    @staticmethod
+    def forward(ctx, p: torch.Tensor, plan: Plan):
+        ctx.plan = plan
+        return plan.reconstruct(p.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_f: torch.Tensor):
+        return ctx.plan.adjoint(grad_f.contiguous()), None

@@ -1,0 +1,744 @@
+// pai_api.cu -- plans and entry points of libpai (C ABI declared in include/pai.h).
+//
+// A call of pai_reconstruct runs Algorithm 2 as three stream-ordered stages:
+//   (a) cuFFT real-to-complex lateral transform of every problem (Eq. fft-1a),
+//       layout [row][n] with the halved lateral axis last;
+//   (b) ONE persistent launch of the fused row kernel over every lateral
+//       frequency row of every problem (prescale, oversampled FFT, window
+//       gather, weight: Algorithm 1 + Eq. fft-0), writing the half image
+//       spectrum;
+//   (c) cuFFT complex-to-real inverse transform of every problem (Eq. fft-1).
+// The sequence is captured once per (input, output) pointer pair into a CUDA
+// graph and replayed.  pai_adjoint runs the transposed stages in reverse.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pai.h"
+#include "pai_internal.h"
+
+using namespace pai;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct ProblemHost {
+  pai_geometry g;
+  int M = 0, mshift = 0, H = 0;
+  double c_eff = 0, K_eff = 0, alpha_eff = 0, beta = 0, pred_err = 0;
+  int n1 = 0, n2 = 0, rows = 0, lz = 0, tpr = 0, rpc = 0;
+  size_t data_off = 0, img_off = 0;   // floats into the concatenated data / image
+  size_t pt_off = 0, fh_off = 0;      // complex values into the workspaces
+  size_t pre_off = 0, rowS_off = 0, zt_off = 0;
+  cufftHandle lat_r2c = 0, lat_c2r = 0, img_c2r = 0, img_r2c = 0;
+  bool have_plans = false;
+  size_t data_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nt; }
+  size_t img_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nz; }
+};
+
+struct GraphEntry {
+  const void* in = nullptr;
+  void* out = nullptr;
+  bool adjoint = false;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct pai_plan_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  std::vector<ProblemHost> probs;
+  int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0;
+  size_t smem_fwd = 0, smem_adj = 0;
+  WindowPoly poly{};
+  double beta = 0, pred_err = 0, fit_err = 0;
+  size_t data_total = 0, img_total = 0;
+  long long nodes = 0;
+  int rows_total = 0;
+  // device memory
+  float2* d_pt = nullptr;        // lateral spectra
+  float2* d_fh = nullptr;        // half image spectra
+  float* d_tables = nullptr;     // prescale / rowS / zt, packed (16-byte aligned sections)
+  float2* d_tw = nullptr;
+  RowProblem* d_problems = nullptr;
+  WorkItem* d_items_fwd = nullptr;
+  int nitems_fwd = 0;
+  WorkItem* d_items_adj = nullptr;
+  int nitems_adj = 0;
+  int* d_counter = nullptr;
+  void* d_cufft_work = nullptr;
+  size_t cufft_work = 0;
+  size_t ws_bytes = 0;
+  // host staging for pai_reconstruct_host
+  float* d_stage_in = nullptr;
+  float* d_stage_out = nullptr;
+  bool use_graph = true;
+  std::vector<GraphEntry> graphs;
+  long long own_kernels = 0, fft_execs = 0;
+  int own_kernels_per_call = 0, fft_per_call = 0;
+};
+
+namespace {
+
+pai_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PAI_OK;
+  if (e == cudaErrorMemoryAllocation) return PAI_ERR_OOM;
+  return PAI_ERR_CUDA;
+}
+
+pai_status fft_status(cufftResult r) {
+  if (r == CUFFT_SUCCESS) return PAI_OK;
+  if (r == CUFFT_ALLOC_FAILED) return PAI_ERR_OOM;
+  return PAI_ERR_CUFFT;
+}
+
+#define PAI_TRY(x)                      \
+  do {                                  \
+    pai_status _s = (x);                \
+    if (_s != PAI_OK) return _s;        \
+  } while (0)
+#define PAI_CUDA(x) PAI_TRY(cuda_status(x))
+#define PAI_FFT(x) PAI_TRY(fft_status(x))
+
+bool is_even_pos(int v) { return v >= 2 && (v % 2) == 0; }
+
+pai_status validate(const pai_geometry& g) {
+  if (g.dim != 2 && g.dim != 3) return PAI_ERR_INVALID_ARG;
+  if (!is_even_pos(g.nx) || !is_even_pos(g.nt) || !is_even_pos(g.nz)) return PAI_ERR_INVALID_ARG;
+  if (g.dim == 3 && !is_even_pos(g.ny)) return PAI_ERR_INVALID_ARG;
+  if (!(g.dx > 0) || !(g.dt > 0) || !(g.c > 0) || !(g.dz > 0)) return PAI_ERR_INVALID_ARG;
+  if (g.dim == 3 && !(g.dy > 0)) return PAI_ERR_INVALID_ARG;
+  if (!(g.oversampling == 0 || g.oversampling > 1.0)) return PAI_ERR_INVALID_ARG;
+  if (!(g.K >= 0) || !(g.alpha >= 0)) return PAI_ERR_INVALID_ARG;
+  if (!std::isfinite(g.dx + g.dt + g.c + g.dz + g.oversampling + g.K + g.alpha)) return PAI_ERR_INVALID_ARG;
+  if (g.dim == 3 && !std::isfinite(g.dy)) return PAI_ERR_INVALID_ARG;
+  if (g.nt > (1 << 14)) return PAI_ERR_UNSUPPORTED;  // M <= 32768 (16 values x 1024 threads x 2)
+  return PAI_OK;
+}
+
+int next_pow2(long long v) {
+  int m = 1;
+  while (m < v) m <<= 1;
+  return m;
+}
+
+int ilog2(int v) {
+  int s = 0;
+  while ((1 << s) < v) ++s;
+  return s;
+}
+
+void split_ff(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// Choose M, H, beta for one problem (before the batch shares H and beta).
+pai_status choose_params(ProblemHost& p) {
+  const pai_geometry& g = p.g;
+  const double c_req = g.oversampling > 0 ? g.oversampling : 2.0;
+  long long want = (long long)std::ceil(c_req * g.nt - 1e-9);
+  p.M = std::max(32, next_pow2(want));
+  if (p.M > 16 * 1024) return PAI_ERR_UNSUPPORTED;
+  p.mshift = ilog2(p.M);
+  p.c_eff = (double)p.M / g.nt;
+  if (g.alpha > 0) {
+    p.beta = g.alpha / c_req;
+    if (!(g.alpha < kPi * (2 * c_req - 1))) return PAI_ERR_INVALID_ARG;
+  } else {
+    p.beta = kPi * (2.0 - 1.0 / p.c_eff) * (1.0 - 1e-3);
+  }
+  if (g.K > 0) {
+    p.H = (int)std::ceil(c_req * g.K - 1e-9);
+    if (p.H < 2) p.H = 2;
+    if (p.H > kMaxH) return PAI_ERR_UNSUPPORTED;
+  } else {
+    p.H = 0;
+    for (int h = 2; h <= kMaxH; ++h)
+      if (predicted_error(p.c_eff, h, p.beta) <= 1e-8) { p.H = h; break; }
+    if (!p.H) p.H = kMaxH;
+  }
+  return PAI_OK;
+}
+
+// Lateral axes: (n1, n2) with n2 halved by the R2C transform.
+void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d2) {
+  if (g.dim == 2) {
+    n1 = 1; n2 = g.nx; d1 = 1.0; d2 = g.dx;
+  } else {
+    n1 = g.nx; n2 = g.ny; d1 = g.dx; d2 = g.dy;
+  }
+}
+
+pai_status make_cufft_plans(ProblemHost& p, size_t& work) {
+  const pai_geometry& g = p.g;
+  size_t ws = 0;
+  // lateral R2C / C2R: batch over time samples, element stride nt
+  {
+    int rank = g.dim - 1;
+    int n[2], inem[2], onem[2];
+    if (g.dim == 2) {
+      n[0] = g.nx; inem[0] = g.nx; onem[0] = g.nx / 2 + 1;
+    } else {
+      n[0] = g.nx; n[1] = g.ny; inem[0] = g.nx; inem[1] = g.ny; onem[0] = g.nx; onem[1] = g.ny / 2 + 1;
+    }
+    PAI_FFT(cufftCreate(&p.lat_r2c));
+    PAI_FFT(cufftSetAutoAllocation(p.lat_r2c, 0));
+    PAI_FFT(cufftMakePlanMany(p.lat_r2c, rank, n, inem, g.nt, 1, onem, g.nt, 1, CUFFT_R2C, g.nt, &ws));
+    work = std::max(work, ws);
+    PAI_FFT(cufftCreate(&p.lat_c2r));
+    PAI_FFT(cufftSetAutoAllocation(p.lat_c2r, 0));
+    PAI_FFT(cufftMakePlanMany(p.lat_c2r, rank, n, onem, g.nt, 1, inem, g.nt, 1, CUFFT_C2R, g.nt, &ws));
+    work = std::max(work, ws);
+  }
+  // image C2R / R2C over all axes, natural layout, depth halved
+  {
+    int rank = g.dim;
+    int n[3];
+    if (g.dim == 2) {
+      n[0] = g.nx; n[1] = g.nz;
+    } else {
+      n[0] = g.nx; n[1] = g.ny; n[2] = g.nz;
+    }
+    PAI_FFT(cufftCreate(&p.img_c2r));
+    PAI_FFT(cufftSetAutoAllocation(p.img_c2r, 0));
+    PAI_FFT(cufftMakePlanMany(p.img_c2r, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &ws));
+    work = std::max(work, ws);
+    PAI_FFT(cufftCreate(&p.img_r2c));
+    PAI_FFT(cufftSetAutoAllocation(p.img_r2c, 0));
+    PAI_FFT(cufftMakePlanMany(p.img_r2c, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &ws));
+    work = std::max(work, ws);
+  }
+  p.have_plans = true;
+  return PAI_OK;
+}
+
+void destroy_fft(ProblemHost& p) {
+  if (!p.have_plans) return;
+  if (p.lat_r2c) cufftDestroy(p.lat_r2c);
+  if (p.lat_c2r) cufftDestroy(p.lat_c2r);
+  if (p.img_c2r) cufftDestroy(p.img_c2r);
+  if (p.img_r2c) cufftDestroy(p.img_r2c);
+  p.have_plans = false;
+}
+
+void release(pai_plan_s* P) {
+  if (!P) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (auto& ge : P->graphs)
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  for (auto& p : P->probs) destroy_fft(p);
+  cudaFree(P->d_pt);
+  cudaFree(P->d_fh);
+  cudaFree(P->d_tables);
+  cudaFree(P->d_tw);
+  cudaFree(P->d_problems);
+  if (P->d_items_adj == P->d_items_fwd) P->d_items_adj = nullptr;
+  cudaFree(P->d_items_fwd);
+  cudaFree(P->d_items_adj);
+  cudaFree(P->d_counter);
+  cudaFree(P->d_cufft_work);
+  cudaFree(P->d_stage_in);
+  cudaFree(P->d_stage_out);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  cudaSetDevice(prev);
+  delete P;
+}
+
+pai_status set_fft_streams(pai_plan_s* P, cudaStream_t s) {
+  for (auto& p : P->probs) {
+    PAI_FFT(cufftSetStream(p.lat_r2c, s));
+    PAI_FFT(cufftSetStream(p.lat_c2r, s));
+    PAI_FFT(cufftSetStream(p.img_c2r, s));
+    PAI_FFT(cufftSetStream(p.img_r2c, s));
+  }
+  return PAI_OK;
+}
+
+RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
+  RowLaunch L;
+  L.problems = P->d_problems;
+  L.items = adjoint ? P->d_items_adj : P->d_items_fwd;
+  L.nitems = adjoint ? P->nitems_adj : P->nitems_fwd;
+  L.counter = P->d_counter + (adjoint ? 1 : 0);
+  L.tw = P->d_tw;
+  L.Mmax = P->Mmax;
+  L.H = P->H;
+  return L;
+}
+
+pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads, int ctas, size_t smem) {
+  RowLaunch L = make_launch(P, adjoint);
+  PAI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(int), s));
+  cudaError_t e = adjoint ? launch_row_adjoint(L, P->poly, threads, ctas, smem, s)
+                          : launch_row_forward(L, P->poly, threads, ctas, smem, s);
+  return cuda_status(e);
+}
+
+// Stages (a)-(c) for the forward operator, enqueued on s.
+pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStream_t s, bool spectrum_only) {
+  for (auto& p : P->probs)
+    PAI_FFT(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_p) + p.data_off, (cufftComplex*)(P->d_pt + p.pt_off)));
+  PAI_TRY(enqueue_row(P, false, s, P->threads, P->ctas, P->smem_fwd));
+  if (!spectrum_only)
+    for (auto& p : P->probs)
+      PAI_FFT(cufftExecC2R(p.img_c2r, (cufftComplex*)(P->d_fh + p.fh_off), d_f + p.img_off));
+  return PAI_OK;
+}
+
+pai_status enqueue_adjoint(pai_plan_s* P, const float* d_h, float* d_pbar, cudaStream_t s) {
+  for (auto& p : P->probs)
+    PAI_FFT(cufftExecR2C(p.img_r2c, const_cast<float*>(d_h) + p.img_off, (cufftComplex*)(P->d_fh + p.fh_off)));
+  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj));
+  for (auto& p : P->probs)
+    PAI_FFT(cufftExecC2R(p.lat_c2r, (cufftComplex*)(P->d_pt + p.pt_off), d_pbar + p.data_off));
+  return PAI_OK;
+}
+
+pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != P->device) cudaSetDevice(P->device);
+  pai_status st = PAI_OK;
+  if (!P->use_graph) {
+    st = adjoint ? enqueue_adjoint(P, (const float*)in, (float*)out, P->stream)
+                 : enqueue_forward(P, (const float*)in, (float*)out, P->stream, false);
+  } else {
+    GraphEntry* hit = nullptr;
+    for (auto& ge : P->graphs)
+      if (ge.in == in && ge.out == out && ge.adjoint == adjoint) hit = &ge;
+    if (!hit) {
+      // capture on the private stream (the caller's stream may be the legacy default stream)
+      st = set_fft_streams(P, P->cap_stream);
+      cudaGraph_t graph = nullptr;
+      if (st == PAI_OK) st = cuda_status(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+      if (st == PAI_OK) {
+        pai_status st2 = adjoint ? enqueue_adjoint(P, (const float*)in, (float*)out, P->cap_stream)
+                                 : enqueue_forward(P, (const float*)in, (float*)out, P->cap_stream, false);
+        cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+        st = (st2 != PAI_OK) ? st2 : cuda_status(e);
+      }
+      cudaGraphExec_t exec = nullptr;
+      if (st == PAI_OK) st = cuda_status(cudaGraphInstantiate(&exec, graph, 0));
+      if (graph) cudaGraphDestroy(graph);
+      pai_status st3 = set_fft_streams(P, P->stream);
+      if (st == PAI_OK) st = st3;
+      if (st == PAI_OK) {
+        if (P->graphs.size() >= 8) {
+          cudaGraphExecDestroy(P->graphs.front().exec);
+          P->graphs.erase(P->graphs.begin());
+        }
+        GraphEntry ge;
+        ge.in = in; ge.out = out; ge.adjoint = adjoint; ge.exec = exec;
+        P->graphs.push_back(ge);
+        hit = &P->graphs.back();
+      } else if (exec) {
+        cudaGraphExecDestroy(exec);
+      }
+    }
+    if (st == PAI_OK) st = cuda_status(cudaGraphLaunch(hit->exec, P->stream));
+  }
+  if (st == PAI_OK) {
+    P->own_kernels += P->own_kernels_per_call;
+    P->fft_execs += P->fft_per_call;
+  }
+  if (prev != P->device) cudaSetDevice(prev);
+  return st;
+}
+
+// Plan construction shared by pai_plan and pai_plan_batched.
+pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_s** out) {
+  if (!gs || !out || count < 1) return PAI_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) PAI_TRY(validate(gs[i]));
+  pai_plan_s* P = new (std::nothrow) pai_plan_s();
+  if (!P) return PAI_ERR_OOM;
+  struct Guard {
+    pai_plan_s* p;
+    ~Guard() { if (p) release(p); }
+  } guard{P};
+  PAI_CUDA(cudaGetDevice(&P->device));
+  P->stream = (cudaStream_t)stream;
+  PAI_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  const char* env_graph = std::getenv("PAI_USE_GRAPH");
+  P->use_graph = !(env_graph && env_graph[0] == '0');
+
+  // ---- parameters -------------------------------------------------------
+  P->probs.resize(count);
+  double c_min = 1e30;
+  for (int i = 0; i < count; ++i) {
+    ProblemHost& p = P->probs[i];
+    p.g = gs[i];
+    if (p.g.dim == 2) { p.g.ny = 1; p.g.dy = 1.0; }
+    PAI_TRY(choose_params(p));
+    P->H = std::max(P->H, p.H);
+    P->Mmax = std::max(P->Mmax, p.M);
+    c_min = std::min(c_min, p.c_eff);
+  }
+  // one window shape for the whole plan: common H and beta
+  bool user_alpha = count == 1 && gs[0].alpha > 0;
+  P->beta = user_alpha ? P->probs[0].beta : kPi * (2.0 - 1.0 / c_min) * (1.0 - 1e-3);
+  for (auto& p : P->probs) {
+    p.H = P->H;
+    p.beta = P->beta;
+    p.K_eff = p.H / p.c_eff;
+    p.alpha_eff = p.beta * p.c_eff;
+    if (!(p.alpha_eff > kPi) || !(p.alpha_eff < kPi * (2 * p.c_eff - 1))) return PAI_ERR_INVALID_ARG;
+    p.pred_err = predicted_error(p.c_eff, p.H, p.beta);
+    P->pred_err = std::max(P->pred_err, p.pred_err);
+  }
+  P->fit_err = fit_window(P->H, P->beta, &P->poly);
+  if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
+
+  // ---- CTA shape ----------------------------------------------------------
+  int sms = 0;
+  PAI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+  int smem_optin = 0;
+  PAI_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+  const int tpr_max = P->Mmax / kElemsPerThread;
+  const char* env_t = std::getenv("PAI_THREADS");
+  int threads = env_t ? std::atoi(env_t) : 512;
+  threads = std::max(threads, tpr_max);
+  threads = std::max(threads, 64);
+  // row slots of a CTA must tile it exactly: the CTA size is a power of two
+  if (threads > 1024 || (threads & (threads - 1)) != 0) return PAI_ERR_UNSUPPORTED;
+
+  // ---- layout -------------------------------------------------------------
+  size_t data_off = 0, img_off = 0, pt_off = 0, fh_off = 0, tab_off = 0;
+  auto align4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+  for (auto& p : P->probs) {
+    double d1, d2;
+    lateral_axes(p.g, p.n1, p.n2, d1, d2);
+    p.rows = p.n1 * (p.n2 / 2 + 1);
+    p.lz = p.g.nz / 2 + 1;
+    p.tpr = p.M / kElemsPerThread;
+    p.data_off = data_off;
+    p.img_off = img_off;
+    p.pt_off = pt_off;
+    p.fh_off = fh_off;
+    data_off += p.data_len();
+    img_off += p.img_len();
+    pt_off += (size_t)p.rows * p.g.nt;
+    fh_off += (size_t)p.n1 * p.n2 * p.lz;
+    p.pre_off = tab_off;
+    tab_off = align4(tab_off + p.g.nt);
+    p.rowS_off = tab_off;
+    tab_off = align4(tab_off + 2 * (size_t)p.rows);
+    p.zt_off = tab_off;
+    tab_off = align4(tab_off + 4 * (size_t)p.lz);
+    P->rows_total += p.rows;
+    const int half = p.n2 / 2;
+    long long mirror_rows = (long long)p.n1 * std::max(0, half - 1);
+    long long plain_rows = (long long)p.rows - mirror_rows;
+    P->nodes += mirror_rows * (long long)p.g.nz + plain_rows * (long long)(p.g.nz / 2 + 1);
+  }
+  P->data_total = data_off;
+  P->img_total = img_off;
+
+  // ---- tables (FP64 on the host) ------------------------------------------
+  std::vector<float> tables(tab_off, 0.0f);
+  for (auto& p : P->probs) {
+    prescale_table(p.g.nt, p.c_eff, p.H, p.beta, 1.0, &tables[p.pre_off]);
+    double d1, d2;
+    int n1, n2;
+    lateral_axes(p.g, n1, n2, d1, d2);
+    const int half = n2 / 2;
+    for (int r = 0; r < p.rows; ++r) {
+      int i1 = r / (half + 1), i2 = r % (half + 1);
+      int k1 = (i1 < n1 / 2 || n1 == 1) ? i1 : i1 - n1;
+      if (n1 == 1) k1 = 0;
+      double a1 = k1 / (n1 * d1), a2 = i2 / (n2 * d2);
+      double S = a1 * a1 + a2 * a2;
+      split_ff(S, tables[p.rowS_off + 2 * r], tables[p.rowS_off + 2 * r + 1]);
+    }
+    for (int l = 0; l < p.lz; ++l) {
+      double kz = l / (p.g.nz * p.g.dz);
+      float hi, lo;
+      split_ff(kz * kz, hi, lo);
+      tables[p.zt_off + 4 * l] = hi;
+      tables[p.zt_off + 4 * l + 1] = lo;
+      tables[p.zt_off + 4 * l + 2] = (float)kz;
+      tables[p.zt_off + 4 * l + 3] = 0.0f;
+    }
+  }
+  std::vector<float2> tw(P->Mmax);
+  for (int k = 0; k < P->Mmax; ++k) {
+    double a = -2.0 * kPi * k / P->Mmax;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+
+  // ---- device memory ------------------------------------------------------
+  PAI_CUDA(cudaMalloc(&P->d_pt, std::max<size_t>(pt_off, 1) * sizeof(float2)));
+  PAI_CUDA(cudaMalloc(&P->d_fh, std::max<size_t>(fh_off, 1) * sizeof(float2)));
+  PAI_CUDA(cudaMalloc(&P->d_tables, std::max<size_t>(tab_off, 4) * sizeof(float)));
+  PAI_CUDA(cudaMalloc(&P->d_tw, P->Mmax * sizeof(float2)));
+  PAI_CUDA(cudaMalloc(&P->d_problems, count * sizeof(RowProblem)));
+  PAI_CUDA(cudaMalloc(&P->d_counter, 4 * sizeof(int)));
+  PAI_CUDA(cudaMemcpy(P->d_tables, tables.data(), tab_off * sizeof(float), cudaMemcpyHostToDevice));
+  PAI_CUDA(cudaMemcpy(P->d_tw, tw.data(), P->Mmax * sizeof(float2), cudaMemcpyHostToDevice));
+  P->ws_bytes = (pt_off + fh_off + P->Mmax) * sizeof(float2) + tab_off * sizeof(float);
+
+  std::vector<RowProblem> rp(count);
+  for (int i = 0; i < count; ++i) {
+    ProblemHost& p = P->probs[i];
+    RowProblem& r = rp[i];
+    r.pt = P->d_pt + p.pt_off;
+    r.fh = P->d_fh + p.fh_off;
+    r.prescale = P->d_tables + p.pre_off;
+    r.rowS = reinterpret_cast<const float2*>(P->d_tables + p.rowS_off);
+    r.zt = reinterpret_cast<const float4*>(P->d_tables + p.zt_off);
+    r.nt = p.g.nt; r.M = p.M; r.nz = p.g.nz; r.lz = p.lz;
+    r.n1 = p.n1; r.n2 = p.n2; r.rows = p.rows;
+    r.tpr = p.tpr;
+    r.mshift = p.mshift;
+    const double B = (double)p.M * p.g.c * p.g.dt;
+    split_ff(B * B, r.B2hi, r.B2lo);
+    r.wscale = (float)(2.0 * p.g.c * p.g.dt / p.g.dz * B / ((double)p.n1 * p.n2 * p.g.nz));
+    r.nt_over_M = (float)((double)p.g.nt / p.M);
+  }
+
+  // ---- cuFFT ----------------------------------------------------------------
+  size_t work = 0;
+  for (auto& p : P->probs) PAI_TRY(make_cufft_plans(p, work));
+  P->cufft_work = work;
+  if (work) {
+    PAI_CUDA(cudaMalloc(&P->d_cufft_work, work));
+    for (auto& p : P->probs) {
+      PAI_FFT(cufftSetWorkArea(p.lat_r2c, P->d_cufft_work));
+      PAI_FFT(cufftSetWorkArea(p.lat_c2r, P->d_cufft_work));
+      PAI_FFT(cufftSetWorkArea(p.img_c2r, P->d_cufft_work));
+      PAI_FFT(cufftSetWorkArea(p.img_r2c, P->d_cufft_work));
+    }
+  }
+  P->ws_bytes += work;
+  PAI_TRY(set_fft_streams(P, P->stream));
+
+  // ---- work items and launch shape ------------------------------------------
+  auto build_items = [&](int T, std::vector<WorkItem>& items) {
+    items.clear();
+    std::vector<std::pair<double, WorkItem>> tmp;
+    for (int i = 0; i < count; ++i) {
+      ProblemHost& p = P->probs[i];
+      const int rpc = T / p.tpr;
+      const double cost = (double)p.M * p.mshift + 2.0 * P->H * p.g.nz;  // per row, rough
+      for (int r0 = 0; r0 < p.rows; r0 += rpc) {
+        WorkItem w;
+        w.problem = i;
+        w.row0 = r0;
+        tmp.push_back({cost * std::min(rpc, p.rows - r0), w});
+      }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const std::pair<double, WorkItem>& a,
+                                                 const std::pair<double, WorkItem>& b) { return a.first > b.first; });
+    for (auto& t : tmp) items.push_back(t.second);
+  };
+  auto finish_shape = [&](int T) -> pai_status {
+    for (int i = 0; i < count; ++i) rp[i].rpc = T / P->probs[i].tpr;
+    int node_cap = 0;
+    for (int i = 0; i < count; ++i) node_cap = std::max(node_cap, rp[i].rpc * (P->probs[i].g.nz + 2));
+    P->threads = T;
+    P->smem_fwd = row_smem_forward(T);
+    P->smem_adj = row_smem_forward(T) + (size_t)node_cap * sizeof(float4);
+    if (P->smem_fwd > (size_t)smem_optin || P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
+    int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H);
+    int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H);
+    if (occ_f < 1 || occ_a < 1) return PAI_ERR_UNSUPPORTED;
+    std::vector<WorkItem> items;
+    build_items(T, items);
+    P->nitems_fwd = P->nitems_adj = (int)items.size();
+    P->ctas = std::min(P->nitems_fwd, occ_f * sms);
+    P->ctas_adj = std::min(P->nitems_adj, occ_a * sms);
+    cudaFree(P->d_items_fwd);
+    P->d_items_fwd = nullptr;
+    PAI_CUDA(cudaMalloc(&P->d_items_fwd, items.size() * sizeof(WorkItem)));
+    PAI_CUDA(cudaMemcpy(P->d_items_fwd, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    P->d_items_adj = P->d_items_fwd;
+    PAI_CUDA(cudaMemcpy(P->d_problems, rp.data(), count * sizeof(RowProblem), cudaMemcpyHostToDevice));
+    return PAI_OK;
+  };
+  // ---- tuner: pick the CTA size by timing the forward row kernel -------------
+  const char* env_tune = std::getenv("PAI_AUTOTUNE");
+  bool tune = !(env_tune && env_tune[0] == '0') && !env_t;
+  if (tune) {
+    int best_T = 0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    PAI_CUDA(cudaEventCreate(&e0));
+    PAI_CUDA(cudaEventCreate(&e1));
+    PAI_CUDA(cudaMemset(P->d_pt, 0, pt_off * sizeof(float2)));
+    for (int T : {256, 512, 1024}) {
+      if (T < tpr_max || T < 64) continue;
+      if (finish_shape(T) != PAI_OK) continue;
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, P->cap_stream);
+        if (enqueue_row(P, false, P->cap_stream, T, P->ctas, P->smem_fwd) != PAI_OK) break;
+        cudaEventRecord(e1, P->cap_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+      }
+      if (best < best_ms) { best_ms = best; best_T = T; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (best_T) threads = best_T;
+  }
+  {
+    // prefer the requested size; fall back to smaller CTAs if shared memory does not fit
+    pai_status st = PAI_ERR_UNSUPPORTED;
+    for (int T = threads; T >= std::max(tpr_max, 32) && st != PAI_OK; T /= 2) st = finish_shape(T);
+    if (st != PAI_OK) return st;
+  }
+  P->ws_bytes += (size_t)P->nitems_fwd * sizeof(WorkItem);
+  P->own_kernels_per_call = 1;       // the row kernel (plus one memset node)
+  P->fft_per_call = 2 * count;
+  PAI_CUDA(cudaDeviceSynchronize());
+  guard.p = nullptr;
+  *out = P;
+  return PAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pai_status pai_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out) {
+  if (!g || !out) return PAI_ERR_INVALID_ARG;
+  return build_plan(g, 1, cuda_stream, out);
+}
+
+pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream, pai_plan_t* out) {
+  if (!g || !out || count < 1) return PAI_ERR_INVALID_ARG;
+  return build_plan(g, count, cuda_stream, out);
+}
+
+pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f) {
+  if (!plan || !d_p || !d_f) return PAI_ERR_INVALID_ARG;
+  return run(plan, d_p, d_f, false);
+}
+
+pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar) {
+  if (!plan || !d_h || !d_pbar) return PAI_ERR_INVALID_ARG;
+  return run(plan, d_h, d_pbar, true);
+}
+
+pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat) {
+  if (!plan || !d_p || !d_fhat) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = enqueue_forward(plan, d_p, nullptr, plan->stream, true);
+  if (st == PAI_OK) {
+    size_t n = 0;
+    for (auto& p : plan->probs) n += (size_t)p.n1 * p.n2 * p.lz;
+    st = cuda_status(cudaMemcpyAsync(d_fhat, plan->d_fh, n * sizeof(float2), cudaMemcpyDeviceToDevice, plan->stream));
+    plan->own_kernels += 1;
+    plan->fft_execs += (long long)plan->probs.size();
+  }
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
+  if (!plan || !h_p || !h_f) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = PAI_OK;
+  if (!plan->d_stage_in) {
+    st = cuda_status(cudaMalloc(&plan->d_stage_in, plan->data_total * sizeof(float)));
+    if (st == PAI_OK) st = cuda_status(cudaMalloc(&plan->d_stage_out, plan->img_total * sizeof(float)));
+  }
+  if (st == PAI_OK)
+    st = cuda_status(cudaMemcpyAsync(plan->d_stage_in, h_p, plan->data_total * sizeof(float),
+                                     cudaMemcpyHostToDevice, plan->stream));
+  if (st == PAI_OK) st = run(plan, plan->d_stage_in, plan->d_stage_out, false);
+  if (st == PAI_OK)
+    st = cuda_status(cudaMemcpyAsync(h_f, plan->d_stage_out, plan->img_total * sizeof(float),
+                                     cudaMemcpyDeviceToHost, plan->stream));
+  if (st == PAI_OK) st = cuda_status(cudaStreamSynchronize(plan->stream));
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream) {
+  if (!plan) return PAI_ERR_INVALID_ARG;
+  plan->stream = (cudaStream_t)cuda_stream;
+  return set_fft_streams(plan, plan->stream);
+}
+
+pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info) {
+  if (!plan || !info) return PAI_ERR_INVALID_ARG;
+  const ProblemHost& p = plan->probs[0];
+  info->count = (int)plan->probs.size();
+  info->M = p.M;
+  info->taps = 2 * plan->H;
+  info->oversampling = p.c_eff;
+  info->K = p.K_eff;
+  info->alpha = p.alpha_eff;
+  info->predicted_error = plan->pred_err;
+  info->threads_per_cta = plan->threads;
+  info->ctas = plan->ctas;
+  info->rows = plan->rows_total;
+  info->nodes = plan->nodes;
+  info->workspace_bytes = plan->ws_bytes;
+  info->uses_graph = plan->use_graph ? 1 : 0;
+  return PAI_OK;
+}
+
+pai_status pai_launch_count(pai_plan_t plan, long long* kernels) {
+  if (!plan || !kernels) return PAI_ERR_INVALID_ARG;
+  *kernels = plan->own_kernels;
+  return PAI_OK;
+}
+
+pai_status pai_destroy(pai_plan_t plan) {
+  if (!plan) return PAI_OK;
+  release(plan);
+  return PAI_OK;
+}
+
+pai_status pai_window_probe(int H, double beta, double c, int n, const double* y, double* phi_out,
+                            double* pred_err, double* fit_err) {
+  if (H < 2 || H > kMaxH || !(c > 1.0) || !(beta * c > kPi) || !(beta * c <= kPi * (2 * c - 1) * (1 + 1e-12)) || n < 0)
+    return PAI_ERR_INVALID_ARG;
+  if (n > 0 && (!y || !phi_out)) return PAI_ERR_INVALID_ARG;
+  const double peak = kb_phi(0.0, H, beta);
+  for (int i = 0; i < n; ++i) phi_out[i] = kb_phi(y[i], H, beta) / peak;
+  if (pred_err) *pred_err = predicted_error(c, H, beta);
+  if (fit_err) {
+    WindowPoly w;
+    *fit_err = fit_window(H, beta, &w);
+  }
+  return PAI_OK;
+}
+
+const char* pai_status_string(pai_status s) {
+  switch (s) {
+    case PAI_OK: return "success";
+    case PAI_ERR_INVALID_ARG: return "invalid argument";
+    case PAI_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PAI_ERR_OOM: return "out of memory";
+    case PAI_ERR_CUDA: return "CUDA error";
+    case PAI_ERR_CUFFT: return "cuFFT error";
+    case PAI_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// pai_internal.h -- descriptors shared by the host planner and the sm_103a
+// kernels of libpai.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pai {
+
+// Largest half tap count supported by the row kernels: taps per node = 2H <= 24.
+constexpr int kMaxH = 12;
+// Polynomial degree of each tap's window polynomial in z = frac - 1/2.
+// Even part: z^0, z^2, ..., z^8 (5 coefficients); odd part: z^1, ..., z^9.
+constexpr int kDeg = 9;
+constexpr int kHalfCoef = (kDeg + 1) / 2;  // 5
+// Complex values each thread holds during an in-shared-memory FFT pass.
+constexpr int kElemsPerThread = 16;
+
+// Window polynomials, identical for every problem of a plan (the window shape
+// depends only on beta = alpha / c_os and H = c_os * K, both shared by the
+// batch).  Tap it = t + H - 1 (t = -H+1 .. H) and its mirror 2H-1-it share
+// one pair p = min(it, 2H-1-it):
+//   w_it(z)        = E_p(z^2) + z O_p(z^2)
+//   w_{2H-1-it}(z) = E_p(z^2) - z O_p(z^2)
+// Passed by value as a kernel parameter, so the coefficients are
+// constant-bank operands of the FMAs.
+struct WindowPoly {
+  float ce[kMaxH][kHalfCoef];  // even coefficients, lowest degree first
+  float co[kMaxH][kHalfCoef];  // odd coefficients (of z^1, z^3, ...)
+};
+
+// One reconstruction problem as the row kernels see it.  Lateral axes are
+// (n1, n2) with n2 the axis halved by the real-to-complex lateral FFT:
+// 2-D: (1, nx); 3-D: (nx, ny).  Row r = i1 * (n2/2 + 1) + i2.
+struct RowProblem {
+  const float2* pt;        // lateral spectrum rows [rows][nt] (fwd in / adj out)
+  float2* fh;              // image half spectrum [n1*n2][lz] (fwd out / adj in)
+  const float* prescale;   // [nt] window prescale incl. all constant factors
+  const float2* rowS;      // [rows] float-float |K_lat / 2 pi|^2
+  const float4* zt;        // [lz] (az_hi, az_lo, kz, 0): az = kz^2, kz = l/(nz dz)
+  int nt, M, nz, lz;
+  int n1, n2, rows;
+  int tpr;                 // threads per row in the FFT = M / kElemsPerThread
+  int rpc;                 // rows per CTA work item
+  float B2hi, B2lo;        // (M c dt)^2 as float-float: node x = B sqrt(S + az)
+  float wscale;            // 2 c dt/dz * B / (n1 n2 nz): W = wscale * kz / x
+  float nt_over_M;         // for the node phase
+  int mshift;              // log2(M)
+};
+
+struct WorkItem {
+  int problem;  // index into the RowProblem array
+  int row0;     // first row; rows row0 .. min(row0 + rpc, rows) - 1
+};
+
+struct RowLaunch {
+  const RowProblem* problems;  // device array
+  const WorkItem* items;       // device array, ordered by decreasing cost
+  int nitems;
+  int* counter;                // device work counter, zeroed before each launch
+  const float2* tw;            // e^{-2 pi i k / Mmax}, k < Mmax
+  int Mmax;
+  int H;                       // half tap count (taps = 2H)
+};
+
+// Host-side window math (FP64), pai_window.cpp
+double bessel_i0(double x);
+// Normalised window transform in grid units: phi(y) = sinh(beta sqrt(H^2 - y^2)) / sqrt(H^2 - y^2)
+// (analytic continuation sin(...) / ... for |y| > H).
+double kb_phi(double y, double H, double beta);
+// Fit the tap polynomials; returns the max abs fit error relative to phi(0).
+double fit_window(int H, double beta, WindowPoly* out);
+// Truncation error of Fourmont's identity for (c, H, beta), max over theta and offsets.
+double predicted_error(double c, int H, double beta);
+// Prescale for sample n: 1 / (pi I0(H sqrt(beta^2 - (theta_n/c)^2))) * phi(0), theta_n = 2 pi n/nt - pi.
+void prescale_table(int nt, double c, int H, double beta, double extra, float* out);
+
+// Kernel launchers, pai_kernels.cu
+cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
+                               cudaStream_t s);
+cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
+                               cudaStream_t s);
+size_t row_smem_forward(int threads);
+size_t row_smem_adjoint(int threads, int max_nodes_per_row, int rpc_max);
+int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H);
+
+}  // namespace pai

@@ -1,0 +1,48 @@
+// pai_launch.cu -- dispatch of the row kernels to the instantiation units.
+#include "pai_internal.h"
+
+namespace pai {
+
+#define PAI_UNIT(lo)                                                                                          \
+  cudaError_t row_forward_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t);    \
+  cudaError_t row_adjoint_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t);    \
+  int row_occupancy_h##lo(int, bool, int, size_t);
+PAI_UNIT(2)
+PAI_UNIT(5)
+PAI_UNIT(7)
+PAI_UNIT(9)
+
+size_t row_smem_forward(int threads) {
+  return (size_t)threads * kElemsPerThread * 33 / 32 * sizeof(float2);
+}
+
+size_t row_smem_adjoint(int threads, int max_nodes_per_row, int rpc_max) {
+  return row_smem_forward(threads) + (size_t)rpc_max * (size_t)(max_nodes_per_row) * sizeof(float4);
+}
+
+cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
+                               cudaStream_t s) {
+  const int H = L.H;
+  if (H < 5) return row_forward_h2(H, L, w, threads, ctas, smem, s);
+  if (H < 7) return row_forward_h5(H, L, w, threads, ctas, smem, s);
+  if (H < 9) return row_forward_h7(H, L, w, threads, ctas, smem, s);
+  return row_forward_h9(H, L, w, threads, ctas, smem, s);
+}
+
+cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
+                               cudaStream_t s) {
+  const int H = L.H;
+  if (H < 5) return row_adjoint_h2(H, L, w, threads, ctas, smem, s);
+  if (H < 7) return row_adjoint_h5(H, L, w, threads, ctas, smem, s);
+  if (H < 9) return row_adjoint_h7(H, L, w, threads, ctas, smem, s);
+  return row_adjoint_h9(H, L, w, threads, ctas, smem, s);
+}
+
+int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H) {
+  if (H < 5) return row_occupancy_h2(H, adjoint, threads, smem);
+  if (H < 7) return row_occupancy_h5(H, adjoint, threads, smem);
+  if (H < 9) return row_occupancy_h7(H, adjoint, threads, smem);
+  return row_occupancy_h9(H, adjoint, threads, smem);
+}
+
+}  // namespace pai

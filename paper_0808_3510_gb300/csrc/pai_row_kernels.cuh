@@ -1,0 +1,544 @@
+// pai_row_kernels.cuh -- sm_103a row kernels of the NUFFT Fourier reconstruction.
+//
+// One "row" is one lateral frequency K_lat of the detector data after the
+// lateral FFT (Eq. fft-1a).  For every row the forward kernel performs the
+// whole one-dimensional nonuniform FFT of Algorithm 1 plus the weight of
+// Eq. (fft-0) without leaving the SM:
+//
+//   1. prescale (Algorithm 1, division by the window) and zero padding to the
+//      oversampled length M = c nt, written straight into shared memory;
+//   2. the length-M FFT of Eq. (nufft-c), in shared memory (Stockham
+//      autosort, radix 16/8/4/2, each thread holding 16 values in registers
+//      per pass);
+//   3. the truncated window gather of Eq. (nufft-a) at the nodes
+//      omega = c_s sign(Kz) |K| (Eq. dft-2d), multiplied by the weight of
+//      Eq. (fft-0), written to the half image spectrum.
+//
+// The oversampled spectrum of a row therefore never reaches HBM: a row costs
+// one read of its nt complex samples and one write of its nz/2+1 (or twice
+// that) spectrum values.  The adjoint kernel runs the exact transpose of the
+// same steps in reverse order (spread in gather form, inverse FFT, prescale).
+//
+// Conventions fixed by the design (each traced to the paper):
+//  * the constant of Fourmont's identity is 1/(2 pi c) (it is the Fourier
+//    coefficient of a 2 pi c periodic function); it lives in the prescale;
+//  * the phase of the Proposition (Eq. nufft-a) is e^{-i pi (omega - j/c)}:
+//    the e^{+i pi j/c} part is applied by storing sample n at position
+//    n - nt/2 (mod M) before the FFT, the e^{-i pi omega} part once per node;
+//  * taps are wrapped modulo M (the oversampled spectrum is M-periodic by
+//    Eq. nufft-c), so nodes beyond the Nyquist band are handled exactly;
+//  * node positions are computed in float-float arithmetic (about 44
+//    significant bits) because an FP32 node alone would cost 1e-5 relative
+//    error at |omega| ~ 3000.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#pragma once
+#include "pai_internal.h"
+
+namespace pai {
+
+#define PADI(i) ((i) + ((i) >> 5))
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// cos and sin of 2 pi q / 16, q = 0..7
+__host__ __device__ constexpr float cos16(int q) {
+  return q == 0 ? 1.0f : q == 1 ? 0.92387953251128674f : q == 2 ? 0.70710678118654752f
+       : q == 3 ? 0.38268343236508977f : q == 4 ? 0.0f : q == 5 ? -0.38268343236508977f
+       : q == 6 ? -0.70710678118654752f : -0.92387953251128674f;
+}
+__host__ __device__ constexpr float sin16(int q) {
+  return q == 0 ? 0.0f : q == 1 ? 0.38268343236508977f : q == 2 ? 0.70710678118654752f
+       : q == 3 ? 0.92387953251128674f : q == 4 ? 1.0f : q == 5 ? 0.92387953251128674f
+       : q == 6 ? 0.70710678118654752f : 0.38268343236508977f;
+}
+
+// x * e^{-+ 2 pi i q / 16}  (forward: minus sign; INV: plus sign)
+template <int Q, bool INV>
+__device__ __forceinline__ float2 twq(float2 x) {
+  if (Q == 0) return x;
+  if (Q == 4) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+  constexpr float c = cos16(Q);
+  constexpr float s = INV ? sin16(Q) : -sin16(Q);
+  return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+}
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1, k = R >> 1; b < R; b <<= 1, k >>= 1)
+    if (i & b) r |= k;
+  return r;
+}
+
+// Butterfly stage of an in-register radix-2 DIT FFT of size R (data in
+// bit-reversed order).  Stage span m, half h = m/2, twiddle q = k * 16/m.
+template <int R, int M2, int K, bool INV>
+struct Stage {
+  __device__ __forceinline__ static void run(float2 (&a)[R]) {
+    constexpr int h = M2 / 2;
+#pragma unroll
+    for (int g = 0; g < R; g += M2) {
+      float2 u = a[g + K];
+      float2 t = twq<K * (16 / M2), INV>(a[g + K + h]);
+      a[g + K] = cadd(u, t);
+      a[g + K + h] = csub(u, t);
+    }
+    Stage<R, M2, K + 1, INV>::run(a);
+  }
+};
+template <int R, int M2, bool INV>
+struct Stage<R, M2, M2 / 2, INV> {
+  __device__ __forceinline__ static void run(float2 (&)[R]) {}
+};
+
+template <int R, int M2, bool INV>
+struct Stages {
+  __device__ __forceinline__ static void run(float2 (&a)[R]) {
+    Stage<R, M2, 0, INV>::run(a);
+    Stages<R, M2 * 2, INV>::run(a);
+  }
+};
+template <int R, bool INV>
+struct Stages<R, R * 2, INV> {
+  __device__ __forceinline__ static void run(float2 (&)[R]) {}
+};
+
+// v <- DFT_R(v): v[k] = sum_r v[r] e^{-+ 2 pi i r k / R}
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  float2 a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[bitrev<R>(i)] = v[i];
+  Stages<R, 2, INV>::run(a);
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = a[i];
+}
+
+// One in-place Stockham pass of radix R over X[0..M) (padded indexing).
+// Butterfly j (0 <= j < M/R) reads X[j + r M/R], twiddles by
+// e^{-+2 pi i r (j mod Ns) / (Ns R)}, and writes the R outputs to
+// X[(j - j mod Ns) R + (j mod Ns) + r Ns].  All reads of the pass complete
+// (barrier) before any write.
+template <int R, bool INV>
+__device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
+                                         int twstride) {
+  constexpr int NB = kElemsPerThread / R;
+  float2 v[NB][R];
+  const int MR = M / R;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = lane + i * tpr;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = j + r * MR;
+      v[i][r] = X[PADI(idx)];
+    }
+  }
+  __syncthreads();
+  const int tws = (M / (Ns * R)) * twstride;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = lane + i * tpr;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = k * tws;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[r * step]);
+        if (INV) w.y = -w.y;
+        v[i][r] = cmul(v[i][r], w);
+      }
+    }
+    dft_reg<R, INV>(v[i]);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = base + r * Ns;
+      X[PADI(idx)] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Length-M FFT (M = 2^mshift >= 32) of each row slot's X, in shared memory.
+template <bool INV>
+__device__ __forceinline__ void fft_smem(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
+                                         int twstride) {
+  int Ns = 1;
+  int rem = mshift;
+  while (rem >= 4) {
+    fft_pass<16, INV>(X, M, Ns, lane, tpr, tw, twstride);
+    Ns <<= 4;
+    rem -= 4;
+  }
+  if (rem == 3) fft_pass<8, INV>(X, M, Ns, lane, tpr, tw, twstride);
+  else if (rem == 2) fft_pass<4, INV>(X, M, Ns, lane, tpr, tw, twstride);
+  else if (rem == 1) fft_pass<2, INV>(X, M, Ns, lane, tpr, tw, twstride);
+}
+
+// ---------------------------------------------------------------------------
+// Node position x = c omega = B sqrt(S + az) in float-float arithmetic.
+// Returns j0 = floor(x), fr = x - j0 in [0,1), and x0 = FP32 value of x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void node_position(float2 S, float4 zt, float B2hi, float B2lo, int& j0, float& fr,
+                                              float& x0) {
+  // s = S + az (two-sum of the high parts, low parts added)
+  float s_hi = __fadd_rn(S.x, zt.x);
+  float bb = __fsub_rn(s_hi, S.x);
+  float err = __fadd_rn(__fsub_rn(S.x, __fsub_rn(s_hi, bb)), __fsub_rn(zt.x, bb));
+  float s_lo = __fadd_rn(err, __fadd_rn(S.y, zt.y));
+  float t = __fadd_rn(s_hi, s_lo);
+  s_lo = __fsub_rn(s_lo, __fsub_rn(t, s_hi));
+  s_hi = t;
+  // y = B^2 s
+  float p = __fmul_rn(B2hi, s_hi);
+  float e = fmaf(B2hi, s_hi, -p);
+  e = fmaf(B2hi, s_lo, e);
+  e = fmaf(B2lo, s_hi, e);
+  float y_hi = __fadd_rn(p, e);
+  float y_lo = __fsub_rn(e, __fsub_rn(y_hi, p));
+  // x = sqrt(y): FP32 root plus one Newton correction from the exact residual
+  x0 = __fsqrt_rn(y_hi);
+  float q = __fmul_rn(x0, x0);
+  float qe = fmaf(x0, x0, -q);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(y_hi, q), qe), y_lo);
+  float delta = r * (0.5f / x0);
+  float fl = floorf(x0);
+  j0 = (int)fl;
+  fr = __fadd_rn(__fsub_rn(x0, fl), delta);
+  if (fr < 0.0f) {
+    fr += 1.0f;
+    j0 -= 1;
+  } else if (fr >= 1.0f) {
+    fr -= 1.0f;
+    j0 += 1;
+  }
+}
+
+__device__ __forceinline__ void negate_node(int j0p, float frp, int& j0, float& fr) {
+  if (frp > 0.0f) {
+    j0 = -j0p - 1;
+    fr = 1.0f - frp;
+  } else {
+    j0 = -j0p;
+    fr = 0.0f;
+  }
+}
+
+// e^{+i pi nu} for nu = (j0 + fr) nt / M, returned as (cos, sin)
+__device__ __forceinline__ float2 node_phase(int j0, float fr, int nt, int M, float nt_over_M) {
+  const int m2 = (int)(((long long)j0 * (long long)nt) & (2LL * M - 1));
+  float s1, c1, s2, c2;
+  sincospif((float)m2 / (float)M, &s1, &c1);
+  sincospif(fr * nt_over_M, &s2, &c2);
+  return make_float2(c1 * c2 - s1 * s2, s1 * c2 + c1 * s2);
+}
+
+// All 2H tap weights of a node with fraction fr (constant-bank coefficients).
+template <int H>
+__device__ __forceinline__ void tap_weights(const WindowPoly& W, float fr, float (&w)[2 * H]) {
+  const float z = fr - 0.5f, z2 = z * z;
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+    for (int e = kHalfCoef - 2; e >= 0; --e) {
+      E = fmaf(E, z2, W.ce[p][e]);
+      O = fmaf(O, z2, W.co[p][e]);
+    }
+    w[p] = fmaf(z, O, E);
+    w[2 * H - 1 - p] = fmaf(-z, O, E);
+  }
+}
+
+// P(nu) = e^{-i pi nu} sum_t w_t G[(j0 + t) mod M], t = -H+1..H   (Eq. nufft-a)
+template <int H>
+__device__ __forceinline__ float2 node_value(const float2* X, const WindowPoly& W, int j0, float fr, int M, int nt,
+                                             float nt_over_M) {
+  float w[2 * H];
+  tap_weights<H>(W, fr, w);
+  const int mask = M - 1;
+  const int base = (j0 - H + 1) & mask;
+  float ax = 0.0f, ay = 0.0f;
+#pragma unroll
+  for (int it = 0; it < 2 * H; ++it) {
+    const int idx = (base + it) & mask;
+    const float2 g = X[PADI(idx)];
+    ax = fmaf(w[it], g.x, ax);
+    ay = fmaf(w[it], g.y, ay);
+  }
+  const float2 ph = node_phase(j0, fr, nt, M, nt_over_M);
+  return make_float2(fmaf(ax, ph.x, ay * ph.y), fmaf(ay, ph.x, -ax * ph.y));
+}
+
+struct RowGeom {
+  int d1, d2;     // destination rows (full lateral index) of +nu and -nu nodes
+  bool mirror;    // row is not self-conjugate: both destinations are written
+  float2 S;       // |K_lat/2pi|^2 as float-float
+};
+
+__device__ __forceinline__ RowGeom row_geom(const RowProblem& P, int row) {
+  RowGeom g;
+  const int half = P.n2 >> 1;
+  const int i1 = row / (half + 1);
+  const int i2 = row - i1 * (half + 1);
+  g.mirror = (i2 > 0) && (i2 < half);
+  g.d1 = i1 * P.n2 + i2;
+  g.d2 = ((P.n1 - i1) % P.n1) * P.n2 + ((P.n2 - i2) % P.n2);
+  g.S = P.rowS[row];
+  return g;
+}
+
+// Node task i of a row: positive l' (1..nz/2-1), negative l' (mirror rows),
+// and one Nyquist task evaluating both nodes at |l'| = nz/2.
+__device__ __forceinline__ void node_task(int i, int nzh, int nA, int& lp, bool& neg, bool& nyq) {
+  neg = false;
+  nyq = false;
+  if (i < nzh - 1) {
+    lp = i + 1;
+  } else if (i == nA - 1) {
+    lp = nzh;
+    nyq = true;
+  } else {
+    lp = i - (nzh - 1) + 1;
+    neg = true;
+  }
+}
+
+template <int H>
+__device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly& W, const float2* X, int row,
+                                           int lane) {
+  const RowGeom rg = row_geom(P, row);
+  const int nzh = P.nz >> 1;
+  const int nA = rg.mirror ? (P.nz - 1) : nzh;
+  float2* out1 = P.fh + (size_t)rg.d1 * P.lz;
+  float2* out2 = P.fh + (size_t)rg.d2 * P.lz;
+  if (lane == 0) {
+    out1[0] = make_float2(0.f, 0.f);
+    if (rg.mirror) out2[0] = make_float2(0.f, 0.f);
+  }
+  for (int i = lane; i < nA; i += P.tpr) {
+    int lp;
+    bool neg, nyq;
+    node_task(i, nzh, nA, lp, neg, nyq);
+    const float4 zt = __ldg(&P.zt[lp]);
+    int j0p, j0;
+    float frp, fr, x0;
+    node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+    const float wt = P.wscale * zt.z / x0;
+    if (!neg) {
+      float2 v = node_value<H>(X, W, j0p, frp, P.M, P.nt, P.nt_over_M);
+      if (nyq) {
+        negate_node(j0p, frp, j0, fr);
+        float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+        float2 a = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
+        out1[lp] = a;
+        if (rg.mirror) out2[lp] = make_float2(a.x, -a.y);
+      } else {
+        out1[lp] = make_float2(wt * v.x, wt * v.y);
+      }
+    } else {
+      negate_node(j0p, frp, j0, fr);
+      float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+      out2[lp] = make_float2(wt * u.x, -wt * u.y);
+    }
+  }
+}
+
+// Fetch the next work item for the whole CTA (dynamic scheduling).
+__device__ __forceinline__ int next_item(int* counter, int* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  return *s_item;
+}
+
+template <int H>
+__global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPoly W) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_item;
+  for (;;) {
+    const int item = next_item(L.counter, &s_item);
+    if (item >= L.nitems) break;
+    const WorkItem wi = L.items[item];
+    const RowProblem& P = L.problems[wi.problem];
+    const int tpr = P.tpr, M = P.M, nt = P.nt;
+    const int slot = threadIdx.x / tpr;
+    const int lane = threadIdx.x - slot * tpr;
+    const int row = wi.row0 + slot;
+    const bool valid = row < P.rows;
+    float2* X = smem + slot * (M + (M >> 5));
+    if (valid) {
+      // prescale + centre: sample n goes to position n - nt/2 (mod M)
+      const float2* src = P.pt + (size_t)row * nt;
+      const int mask = M - 1, h = nt >> 1;
+      for (int n = lane; n < nt; n += tpr) {
+        const float2 v = __ldg(&src[n]);
+        const float s = __ldg(&P.prescale[n]);
+        const int m = (n - h) & mask;
+        X[PADI(m)] = make_float2(s * v.x, s * v.y);
+      }
+      for (int m = h + lane; m < M - h; m += tpr) X[PADI(m)] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_smem<false>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
+    if (valid) gather_row<H>(P, W, X, row, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+
+// One tap weight w_it(fr) from the shared-memory copy of the coefficients.
+template <int H>
+__device__ __forceinline__ float tap_weight(const float* sce, const float* sco, int it, float fr) {
+  const bool lo = it < H;
+  const int p = lo ? it : 2 * H - 1 - it;
+  const float z = lo ? (fr - 0.5f) : (0.5f - fr);
+  const float z2 = z * z;
+  float E = sce[(kHalfCoef - 1) * kMaxH + p], O = sco[(kHalfCoef - 1) * kMaxH + p];
+#pragma unroll
+  for (int e = kHalfCoef - 2; e >= 0; --e) {
+    E = fmaf(E, z2, sce[e * kMaxH + p]);
+    O = fmaf(O, z2, sco[e * kMaxH + p]);
+  }
+  return fmaf(z, O, E);
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
+  return (a >= 0) ? a / b : -((-a + b - 1) / b);
+}
+
+template <int H>
+__global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPoly W, int fft_floats) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_item;
+  __shared__ float sce[kHalfCoef * kMaxH], sco[kHalfCoef * kMaxH];
+  for (int i = threadIdx.x; i < kHalfCoef * kMaxH; i += blockDim.x) {
+    const int e = i / kMaxH, p = i - e * kMaxH;
+    sce[i] = W.ce[p][e];
+    sco[i] = W.co[p][e];
+  }
+  float4* nodes_all = reinterpret_cast<float4*>(smem + fft_floats / 2);
+  for (;;) {
+    const int item = next_item(L.counter, &s_item);
+    if (item >= L.nitems) break;
+    const WorkItem wi = L.items[item];
+    const RowProblem& P = L.problems[wi.problem];
+    const int tpr = P.tpr, M = P.M, nt = P.nt, mask = M - 1;
+    const int slot = threadIdx.x / tpr;
+    const int lane = threadIdx.x - slot * tpr;
+    const int row = wi.row0 + slot;
+    const bool valid = row < P.rows;
+    float2* X = smem + slot * (M + (M >> 5));
+    float4* N = nodes_all + slot * (P.nz + 2);
+    const int nzh = P.nz >> 1;
+    RowGeom rg;
+    int nneg = 1, nn = 0;
+    if (valid) {
+      rg = row_geom(P, row);
+      nneg = rg.mirror ? nzh : 1;
+      nn = nneg + nzh;
+      // phase 1: node values Q = e^{+i pi nu} * Pbar, stored sorted by position
+      const int nA = rg.mirror ? (P.nz - 1) : nzh;
+      const float2* in1 = P.fh + (size_t)rg.d1 * P.lz;
+      const float2* in2 = P.fh + (size_t)rg.d2 * P.lz;
+      for (int i = lane; i < nA; i += tpr) {
+        int lp;
+        bool neg, nyq;
+        node_task(i, nzh, nA, lp, neg, nyq);
+        const float4 zt = __ldg(&P.zt[lp]);
+        int j0p, j0;
+        float frp, fr, x0;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+        const float wt = P.wscale * zt.z / x0;
+        negate_node(j0p, frp, j0, fr);
+        if (nyq) {
+          float2 y = in1[lp];
+          if (rg.mirror) {
+            const float2 y2 = in2[lp];
+            y.x += y2.x;
+            y.y -= y2.y;
+          }
+          const float2 pb = make_float2(0.5f * wt * y.x, 0.5f * wt * y.y);
+          const float2 php = node_phase(j0p, frp, nt, M, P.nt_over_M);
+          const float2 phn = node_phase(j0, fr, nt, M, P.nt_over_M);
+          const float2 qp = cmul(pb, php), qn = cmul(pb, phn);
+          N[nneg + nzh - 1] = make_float4(__int_as_float(j0p), frp, qp.x, qp.y);
+          N[0] = make_float4(__int_as_float(j0), fr, qn.x, qn.y);
+        } else if (!neg) {
+          const float2 y = in1[lp];
+          const float2 pb = make_float2(2.0f * wt * y.x, 2.0f * wt * y.y);
+          const float2 q = cmul(pb, node_phase(j0p, frp, nt, M, P.nt_over_M));
+          N[nneg + lp - 1] = make_float4(__int_as_float(j0p), frp, q.x, q.y);
+        } else {
+          const float2 y = in2[lp];
+          const float2 pb = make_float2(2.0f * wt * y.x, -2.0f * wt * y.y);
+          const float2 q = cmul(pb, node_phase(j0, fr, nt, M, P.nt_over_M));
+          N[nzh - lp] = make_float4(__int_as_float(j0), fr, q.x, q.y);
+        }
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      // phase 2: grid point j sums w_{j - j0}(fr) Q over nodes with j0 in [j - H, j + H - 1],
+      // including the periodic images j + m M.  Each thread owns 16 consecutive points.
+      const int a = lane * kElemsPerThread;
+      const int j0min = __float_as_int(N[0].x), j0max = __float_as_int(N[nn - 1].x);
+      float2 acc[kElemsPerThread];
+#pragma unroll
+      for (int q = 0; q < kElemsPerThread; ++q) acc[q] = make_float2(0.f, 0.f);
+      const int mlo = -floor_div(-(j0min - H - (kElemsPerThread - 2) - a), M);
+      const int mhi = floor_div(j0max + H - a, M);
+      for (int m = mlo; m <= mhi; ++m) {
+        const int g0 = a + m * M;
+        // first node with j0 >= g0 - H
+        int lo = 0, hi = nn;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (__float_as_int(N[mid].x) < g0 - H) lo = mid + 1;
+          else hi = mid;
+        }
+        int klo = lo, khi = lo;
+#pragma unroll
+        for (int q = 0; q < kElemsPerThread; ++q) {
+          const int g = g0 + q;
+          while (klo < nn && __float_as_int(N[klo].x) < g - H) ++klo;
+          if (khi < klo) khi = klo;
+          while (khi < nn && __float_as_int(N[khi].x) <= g + H - 1) ++khi;
+          float2 s = acc[q];
+          for (int k = klo; k < khi; ++k) {
+            const float4 nd = N[k];
+            const float w = tap_weight<H>(sce, sco, g - __float_as_int(nd.x) + H - 1, nd.y);
+            s.x = fmaf(w, nd.z, s.x);
+            s.y = fmaf(w, nd.w, s.y);
+          }
+          acc[q] = s;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kElemsPerThread; ++q) X[PADI(a + q)] = acc[q];
+    }
+    __syncthreads();
+    fft_smem<true>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
+    if (valid) {
+      const float scale = rg.mirror ? 0.5f : 1.0f;
+      float2* dst = const_cast<float2*>(P.pt) + (size_t)row * nt;
+      const int h = nt >> 1;
+      for (int n = lane; n < nt; n += tpr) {
+        const float2 v = X[PADI((n - h) & mask)];
+        const float s = scale * __ldg(&P.prescale[n]);
+        dst[n] = make_float2(s * v.x, s * v.y);
+      }
+    }
+  }
+}
+
+}  // namespace pai

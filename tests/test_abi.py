@@ -1,0 +1,95 @@
+"""The C-ABI library: it builds, loads, exports every symbol include/pai.h
+declares, validates arguments on the host, and its plan-time window math
+matches the paper's printed constants.  No GPU work is issued here."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pai():
+    from paper_0808_3510_gb300 import build
+    build.build()
+    import paper_0808_3510_gb300 as m
+    return m
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "pai.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pai_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("pai_plan", "pai_plan_batched", "pai_reconstruct", "pai_adjoint", "pai_destroy",
+                     "pai_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pai):
+    lib = ctypes.CDLL(pai.library_path())
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(pai):
+    lib = pai.load_library()
+    for s in range(7):
+        assert lib.pai_status_string(s)
+    assert lib.pai_status_string(99) == b"unknown status"
+
+
+def test_destroy_null_is_ok(pai):
+    assert pai.load_library().pai_destroy(None) == 0
+
+
+@pytest.mark.parametrize("field,value", [
+    ("dim", 4), ("nx", 7), ("nx", 0), ("nt", 9), ("nz", -2), ("dx", 0.0), ("dt", -1.0), ("c", 0.0),
+    ("dz", float("nan")), ("oversampling", 1.0), ("oversampling", 0.5), ("K", -1.0),
+])
+def test_invalid_geometry_rejected_on_host(pai, field, value):
+    """Validation happens before any CUDA call, so it is testable without a GPU."""
+    g = pai.geometry(dict(dim=2, nx=16, nt=32, nz=16))
+    setattr(g, field, value)
+    h = ctypes.c_void_p()
+    assert pai.load_library().pai_plan(ctypes.byref(g), None, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_invalid_pointers_rejected(pai):
+    lib = pai.load_library()
+    assert lib.pai_plan(None, None, None) == 1
+    assert lib.pai_reconstruct(None, None, None) == 1
+    assert lib.pai_adjoint(None, None, None) == 1
+    assert lib.pai_plan_batched(None, 0, None, None) == 1
+
+
+def test_window_matches_paper_constants(pai):
+    """Sec. 3.2: |psi_hat(K)/psi_hat(0)| ~ 3e-11 for K = 3, alpha = 3 pi (c = 2:
+    H = cK = 6, beta = alpha/c = 1.5 pi), and the truncation error of Fourmont's
+    identity stays below the paper's quoted bound 3e-8."""
+    phi, pred, fit = pai.window_probe(6, 1.5 * math.pi, 2.0, [0.0, 6.0, -6.0, 2.5, -2.5])
+    assert phi[0] == 1.0
+    assert abs(phi[1] / 2.97e-11 - 1) < 0.01 and phi[1] == phi[2] and phi[3] == phi[4]
+    assert pred < 3e-8
+    assert fit < 1e-7
+
+
+def test_window_truncation_error_falls_with_taps(pai):
+    errs = [pai.window_probe(H, 1.5 * math.pi * 0.999, 2.0, [])[1] for H in range(2, 9)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[4] < 1e-9          # K = 3 (12 taps)
+    assert errs[6] < 1e-12         # K = 4 (16 taps)
+
+
+def test_window_probe_rejects_lemma_violations(pai):
+    lib = pai.load_library()
+    assert lib.pai_window_probe(6, 2.0 * math.pi, 2.0, 0, None, None, None, None) == 1   # alpha > pi(2c-1)
+    assert lib.pai_window_probe(1, 1.5 * math.pi, 2.0, 0, None, None, None, None) == 1
+    assert lib.pai_window_probe(6, 1.5 * math.pi, 1.0, 0, None, None, None, None) == 1

@@ -1,0 +1,104 @@
+"""The GPU adjoint (pai_adjoint) and the autograd wrapper.
+
+Checks: the dot-product identity <R p, h> = <p, R^T h> between the GPU
+forward and the GPU adjoint (1e-6), the GPU adjoint against the oracle's exact
+transpose (1e-5), gradients through PAIRecon against R^T(R p - f) and against
+central finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as ph
+from gpu_common import DOT_TOL, TOL, gdict, pai, rel, to_gpu, to_np  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+    ph.Geometry(dim=2, nx=300, nt=700, nz=350, dx=1.0, dt=0.5, c=1.5, dz=0.8),
+    ph.Geometry(dim=2, nx=6, nt=10, nz=4),
+    ph.Geometry(dim=3, nx=20, ny=12, nt=48, nz=18, dx=0.9, dy=1.1, dt=0.7, c=1.3, dz=1.0),
+    ph.Geometry(dim=3, nx=32, ny=32, nt=64, nz=32),
+]
+
+
+@pytest.mark.parametrize("g", CASES, ids=lambda g: f"{g.dim}d-{g.nx}x{g.ny}x{g.nt}-{g.nz}")
+def test_dot_product_identity(pai, g):
+    plan = pai.Plan(gdict(g, K=3))
+    p = ph.random_data(50, g)
+    h = ph.random_image(51, g)
+    Rp = to_np(plan.reconstruct(to_gpu(p)))
+    Rth = to_np(plan.adjoint(to_gpu(h)))
+    p32 = p.astype(np.float32).astype(np.float64)
+    h32 = h.astype(np.float32).astype(np.float64)
+    lhs = float(np.vdot(Rp, h32))
+    rhs = float(np.vdot(p32, Rth))
+    scale = np.linalg.norm(Rp) * np.linalg.norm(h32)
+    assert abs(lhs - rhs) < DOT_TOL * scale
+
+
+@pytest.mark.parametrize("g", CASES, ids=lambda g: f"{g.dim}d-{g.nx}x{g.ny}x{g.nt}-{g.nz}")
+def test_adjoint_against_oracle(pai, g):
+    plan = pai.Plan(gdict(g, K=3))
+    h = ph.random_image(52, g).astype(np.float32)
+    got = to_np(plan.adjoint(to_gpu(h)))
+    ref = oracle.adjoint(g, h.astype(np.float64))
+    assert rel(got, ref) < TOL
+
+
+def test_adjoint_batched(pai):
+    geoms = [ph.Geometry(dim=2, nx=64, nt=130, nz=64), ph.Geometry(dim=2, nx=36, nt=512, nz=100),
+             ph.Geometry(dim=3, nx=10, ny=8, nt=40, nz=16)]
+    plan = pai.Plan([gdict(g, K=3) for g in geoms])
+    hs = [ph.random_image(60 + i, g).astype(np.float32) for i, g in enumerate(geoms)]
+    out = to_np(plan.adjoint(to_gpu(np.concatenate([h.ravel() for h in hs]))))
+    off = 0
+    for g, h in zip(geoms, hs):
+        n = g.nx * g.ny * g.nt
+        assert rel(out[off: off + n].reshape(g.data_shape), oracle.adjoint(g, h.astype(np.float64))) < TOL
+        off += n
+
+
+def test_autograd_gradient_is_adjoint_of_residual(pai):
+    import torch
+    g = ph.Geometry(dim=3, nx=24, ny=24, nt=48, nz=24)
+    prob_p = ph.random_data(70, g)
+    f_true = ph.random_image(71, g)
+    plan = pai.Plan(gdict(g, K=3))
+    p = to_gpu(prob_p).requires_grad_(True)
+    ft = to_gpu(f_true)
+    loss = 0.5 * ((pai.PAIRecon.apply(p, plan) - ft) ** 2).sum()
+    loss.backward()
+    with torch.no_grad():
+        expect = plan.adjoint(plan.reconstruct(p.detach()) - ft)
+    torch.cuda.synchronize()
+    assert rel(to_np(p.grad), to_np(expect)) < 1e-6
+
+
+def test_finite_differences(pai):
+    """Central differences with step 1e-3 at 32 random coordinates; the loss is
+    evaluated in FP64 from FP32 reconstructions as <a-b, (a+b)/2> - <a-b, f>."""
+    import torch
+    g = ph.Geometry(dim=3, nx=24, ny=24, nt=48, nz=24)
+    plan = pai.Plan(gdict(g, K=3))
+    p0 = ph.random_data(72, g).astype(np.float32)
+    f_true = ph.random_image(73, g)
+    pt = to_gpu(p0).requires_grad_(True)
+    loss = 0.5 * ((pai.PAIRecon.apply(pt, plan) - to_gpu(f_true)) ** 2).sum()
+    loss.backward()
+    grad = to_np(pt.grad).ravel()
+    rng = np.random.default_rng(0)
+    idx = rng.choice(p0.size, 32, replace=False)
+    step = 1e-3
+    fd = []
+    for i in idx:
+        a = p0.ravel().copy()
+        b = p0.ravel().copy()
+        a[i] += step
+        b[i] -= step
+        ra = to_np(plan.reconstruct(to_gpu(a.reshape(g.data_shape)))).ravel()
+        rb = to_np(plan.reconstruct(to_gpu(b.reshape(g.data_shape)))).ravel()
+        d = ra - rb
+        fd.append((np.dot(d, 0.5 * (ra + rb)) - np.dot(d, f_true.ravel())) / (2 * step))
+    fd = np.array(fd)
+    assert rel(fd, grad[idx]) < 1e-3

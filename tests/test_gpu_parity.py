@@ -1,0 +1,184 @@
+"""GPU reconstruction (libpai through its C ABI) against the FP64 oracle.
+
+Every case feeds the oracle the same FP32-rounded data the GPU sees, so the
+difference measures the GPU path alone.  Bar: relative L2 <= 1e-5 (FP32
+arithmetic; the FP64 NUFFT truncation error of the chosen windows is below
+1e-9, so the bar is set by rounding)."""
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as ph
+from gpu_common import TOL, gdict, oracle_half_spectrum, pai, rel, to_gpu, to_np  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _recon(pai, g, p, **over):
+    import torch
+    plan = pai.Plan(gdict(g, **over))
+    f = to_np(plan.reconstruct(to_gpu(p)))
+    return f, plan
+
+
+def _ref(g, p):
+    return oracle.reconstruct(g, np.asarray(p, dtype=np.float32).astype(np.float64))
+
+
+def test_plain_2d_128x256(pai):
+    """2-D line detector, 128 detectors x 256 samples -> 128 x 128 (c = 2, K = 3)."""
+    prob = ph.plain_2d(0)
+    f, plan = _recon(pai, prob.geom, prob.p, oversampling=2, K=3)
+    info = plan.info
+    assert info["M"] == 512 and info["taps"] == 12
+    assert rel(f, _ref(prob.geom, prob.p)) < TOL
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_plain_2d_more_seeds_and_auto_window(pai, seed):
+    prob = ph.plain_2d(seed)
+    f, _ = _recon(pai, prob.geom, prob.p)
+    assert rel(f, _ref(prob.geom, prob.p)) < TOL
+
+
+def test_2d_general_grid_ragged(pai):
+    """nt not a power of two (M = 2048, effective c = 2.93), nx with a ragged last
+    work item, c != 1, dt != dx, dz != dx."""
+    g = ph.Geometry(dim=2, nx=300, nt=700, nz=350, dx=1.0, dt=0.5, c=1.5, dz=0.8)
+    p = ph.random_data(21, g)
+    f, plan = _recon(pai, g, p, K=3)
+    assert plan.info["M"] == 2048
+    assert rel(f, _ref(g, p)) < TOL
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (4, 8, 6), (6, 4, 10), (16, 34, 12)])
+def test_2d_tiny_and_degenerate(pai, shape):
+    nx, nt, nz = shape
+    g = ph.Geometry(dim=2, nx=nx, nt=nt, nz=nz)
+    p = ph.random_data(22, g)
+    f, _ = _recon(pai, g, p)
+    assert rel(f, _ref(g, p)) < TOL
+
+
+@pytest.mark.parametrize("K,os_", [(4, 2), (3, 3), (2, 2), (1.5, 4)])
+def test_2d_window_parameters(pai, K, os_):
+    g = ph.Geometry(dim=2, nx=64, nt=200, nz=96)
+    p = ph.random_data(23, g)
+    f, plan = _recon(pai, g, p, K=K, oversampling=os_)
+    assert plan.info["predicted_error"] < 1e-6
+    assert rel(f, _ref(g, p)) < TOL
+
+
+def test_3d_general_grid(pai):
+    g = ph.Geometry(dim=3, nx=20, ny=12, nt=48, nz=18, dx=0.9, dy=1.1, dt=0.7, c=1.3, dz=1.0)
+    p = ph.random_data(24, g)
+    f, _ = _recon(pai, g, p, K=3)
+    assert rel(f, _ref(g, p)) < TOL
+
+
+def test_3d_planar_128(pai):
+    """3-D planar: 128 x 128 detectors x 256 samples -> 128^3, uniform balls."""
+    prob = ph.planar_3d(0)
+    f, plan = _recon(pai, prob.geom, prob.p, oversampling=2, K=3)
+    assert rel(f, _ref(prob.geom, prob.p)) < TOL
+
+
+def test_spectrum_stage_against_oracle(pai):
+    """Steps 1-3 alone (lateral FFT, NUFFT, weight) against the oracle spectrum."""
+    for g in (ph.Geometry(dim=2, nx=40, nt=100, nz=60, dz=0.9),
+              ph.Geometry(dim=3, nx=10, ny=14, nt=40, nz=20, dy=1.2)):
+        p = ph.random_data(25, g)
+        plan = pai.Plan(gdict(g, K=3))
+        S = plan.spectrum(to_gpu(p)).cpu().numpy()
+        F = oracle.spectrum(g, np.asarray(p, np.float32).astype(np.float64))
+        assert rel(S, oracle_half_spectrum(g, F)) < TOL
+
+
+def test_input_preserved_and_repeatable(pai):
+    import torch
+    prob = ph.plain_2d(3)
+    plan = pai.Plan(gdict(prob.geom))
+    p = to_gpu(prob.p)
+    keep = p.clone()
+    a = plan.reconstruct(p)
+    b = plan.reconstruct(p)
+    torch.cuda.synchronize()
+    assert torch.equal(p, keep)
+    assert torch.equal(a, b)
+
+
+def test_graph_cache_distinct_buffers(pai):
+    import torch
+    g = ph.Geometry(dim=2, nx=32, nt=64, nz=32)
+    plan = pai.Plan(gdict(g))
+    p1, p2 = to_gpu(ph.random_data(26, g)), to_gpu(ph.random_data(27, g))
+    o1, o2 = plan.reconstruct(p1), plan.reconstruct(p2)
+    o1b = plan.reconstruct(p1)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o1b)
+    assert rel(to_np(o2), _ref(g, ph.random_data(27, g))) < TOL
+
+
+def test_reconstruct_host_matches_device(pai):
+    import torch
+    prob = ph.plain_2d(4)
+    plan = pai.Plan(gdict(prob.geom))
+    host = torch.from_numpy(prob.p.astype(np.float32)).pin_memory()
+    fh = plan.reconstruct_host(host)
+    fd = plan.reconstruct(host.cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(fh, fd.cpu())
+
+
+def test_bad_tensors_rejected(pai):
+    import torch
+    g = ph.Geometry(dim=2, nx=16, nt=32, nz=16)
+    plan = pai.Plan(gdict(g))
+    with pytest.raises(ValueError):
+        plan.reconstruct(torch.zeros(16, 31, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.reconstruct(torch.zeros(16, 32, device="cuda", dtype=torch.float64))
+    with pytest.raises(ValueError):
+        plan.reconstruct(torch.zeros(32, 16, device="cuda").t())
+
+
+def test_batched_uneven_matches_oracle_and_single_plans(pai):
+    import torch
+    geoms = [ph.Geometry(dim=2, nx=64, nt=130, nz=64), ph.Geometry(dim=2, nx=36, nt=512, nz=100),
+             ph.Geometry(dim=2, nx=128, nt=66, nz=34, dt=0.8), ph.Geometry(dim=3, nx=10, ny=8, nt=40, nz=16)]
+    ps = [ph.random_data(30 + i, g) for i, g in enumerate(geoms)]
+    plan = pai.Plan([gdict(g, K=3) for g in geoms])
+    flat = np.concatenate([p.ravel() for p in ps])
+    out = to_np(plan.reconstruct(to_gpu(flat)))
+    off = 0
+    for g, p in zip(geoms, ps):
+        n = g.voxels
+        f = out[off: off + n].reshape(g.image_shape)
+        off += n
+        assert rel(f, _ref(g, p)) < TOL
+    assert off == out.size
+
+
+def test_large_2d_sampled_rows(pai):
+    """2-D large (2048 x 4096 -> 2048 x 2048, c = 2, K = 4) in the launch
+    configuration the benchmark times: sampled spectrum rows against the
+    oracle's row-by-row direct sums, and the image against an FP64 inverse FFT
+    of the GPU's own spectrum (checks the inverse stage at full size)."""
+    import torch
+    g = ph.Geometry(dim=2, nx=2048, nt=4096, nz=2048)
+    p = ph.random_data(40, g).astype(np.float32)
+    plan = pai.Plan(gdict(g, oversampling=2, K=4))
+    assert plan.info["M"] == 8192 and plan.info["taps"] == 16
+    pt = to_gpu(p)
+    S = plan.spectrum(pt).cpu().numpy()
+    ks = np.array([0, 1, 2, 37, 511, 1023, 1024, -1, -2, -700, -1023])
+    F = oracle.spectrum_rows(g, p.astype(np.float64), ks)
+    nzh = g.nz // 2
+    Fneg = oracle.spectrum_rows(g, p.astype(np.float64), -ks)
+    for r, k in enumerate(ks):
+        exp = F[r, : nzh + 1].copy() / (g.nx * g.nz)
+        exp[nzh] = 0.5 * (F[r, nzh] + np.conj(Fneg[r, nzh])) / (g.nx * g.nz)
+        assert rel(S[k % g.nx], exp) < TOL, k
+    f = to_np(plan.reconstruct(pt))
+    ref = np.fft.irfft2(S.astype(np.complex128) * (g.nx * g.nz), s=(g.nx, g.nz))
+    assert rel(f, ref) < TOL
