@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 NUFFT Fourier reconstruction (libpai).
+
+Metric: reconstructed voxels per second (whole job, all ranks), inputs already
+resident in HBM, one step = one pai_reconstruct of one problem (or of the whole
+batch for --config batched2d).  L2 is flushed (512 MiB write) before every
+timed step; each step is timed with CUDA events on the launching stream.
+
+Also reported on the same JSON line:
+  roofline      the row kernel (the dominant hand-written kernel): algorithmic
+                bytes per launch / its event-timed duration vs the measured HBM
+                copy bandwidth, plus the ncu DRAM traffic recorded for it;
+  e2e           the same metric through pai_reconstruct_host (pinned host
+                buffers, H2D and D2H copies inside the timed region);
+  cpu_baseline  the FP64 oracle (direct Fourier reconstruction) timed on this
+                host's cores on a bounded sample of the same workload;
+  clocks        nvidia-smi SM clock and throttle reasons sampled while timing.
+
+``--impl reference`` times the oracle alone (the reference arm) on the same
+workload, metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstructed voxels/s and NUFFT-kernel HBM GB/s at rel L2<=1e-5, batched vs plain"
+UNIT = "voxels/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def workload(name: str, seed: int = 0):
+    """Returns (description, list of geometry dicts, list of float32 data arrays)."""
+    import phantoms as ph
+
+    def gd(g, **kw):
+        d = dict(dim=g.dim, nx=g.nx, ny=g.ny, dx=g.dx, dy=g.dy, nt=g.nt, dt=g.dt, c=g.c, nz=g.nz, dz=g.dz)
+        d.update(kw)
+        return d
+
+    if name == "large2d":
+        pr = ph.large_2d(seed)
+        return ("2-D line detector: 2048 detectors x 4096 samples -> 2048 x 2048 image, 50 f_circ discs "
+                "(closed-form data) + white noise at 1% of peak; oversampling 2, K = 4 (16 taps)",
+                [gd(pr.geom, oversampling=2.0, K=4.0)], [pr.p.astype(np.float32)])
+    if name == "plain2d":
+        pr = ph.plain_2d(seed)
+        return ("2-D line detector: 128 detectors x 256 samples -> 128 x 128, 1-8 uniform discs (spectral "
+                "propagation); oversampling 2, K = 3 (12 taps)",
+                [gd(pr.geom, oversampling=2.0, K=3.0)], [pr.p.astype(np.float32)])
+    if name == "planar3d":
+        pr = ph.planar_3d(seed)
+        return ("3-D planar detector: 128 x 128 detectors x 256 samples -> 128^3, 1-20 uniform balls (N-waves); "
+                "oversampling 2, K = 3", [gd(pr.geom, oversampling=2.0, K=3.0)], [pr.p.astype(np.float32)])
+    if name == "adjoint3d":
+        pr = ph.adjoint_3d(seed)
+        return ("3-D planar detector: 256 x 256 detectors x 512 samples -> 256^3, uniform balls; oversampling 2, K = 3",
+                [gd(pr.geom, oversampling=2.0, K=3.0)], [pr.p.astype(np.float32)])
+    if name == "batched2d":
+        probs = ph.batched_2d(seed)
+        return ("64 uneven 2-D problems (nx = 2 U{128..1024}, nt = 2 U{256..2048}, nz = nt/2) in one plan; "
+                "f_circ disc phantoms; window chosen by the planner (truncation error <= 1e-8)",
+                [gd(p.geom) for p in probs], [p.p.astype(np.float32) for p in probs])
+    raise SystemExit(f"unknown config {name}")
+
+
+def voxels_of(geoms) -> int:
+    return sum(g["nx"] * (g["ny"] if g["dim"] == 3 else 1) * g["nz"] for g in geoms)
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(geoms, datas, target_s: float = 10.0):
+    """Voxels/s of the FP64 oracle, estimated from a bounded sample: direct
+    lateral DFT rows plus direct NUDFT rows (steps 1-3 of the direct Fourier
+    reconstruction) for a subset of lateral frequencies of the first problem,
+    extrapolated to all rows of every problem.  The final inverse DFT is not
+    timed, so the rate is an upper bound on the oracle's speed."""
+    import oracle
+    import phantoms as ph
+
+    g0 = geoms[0]
+    G = ph.Geometry(**{k: g0[k] for k in ("dim", "nx", "ny", "dx", "dy", "nt", "dt", "c", "nz", "dz")})
+    p = datas[0].astype(np.float64).reshape(G.data_shape)
+    rng = np.random.default_rng(1)
+    nrows_total = G.nx * (G.ny if G.dim == 3 else 1)
+
+    def run(nrows):
+        kx = rng.integers(-G.nx // 2, G.nx // 2, nrows)
+        ky = rng.integers(-G.ny // 2, G.ny // 2, nrows) if G.dim == 3 else np.zeros(nrows, int)
+        t = time.perf_counter()
+        oracle.spectrum_rows(G, p, kx, ky)
+        return time.perf_counter() - t
+
+    n = max(1, oracle.threads())
+    t = run(n)
+    per_row = t / n
+    rows = int(min(nrows_total, max(n, target_s / max(per_row, 1e-9))))
+    t = run(rows)
+    per_row = t / rows
+    # every problem costs rows x (nx ny nt + nz nt) in this model; scale by op count
+    def cost(g):
+        nl = g["nx"] * (g["ny"] if g["dim"] == 3 else 1)
+        return nl * (nl * g["nt"] + g["nz"] * g["nt"])
+    est = per_row / (G.nx * (G.ny if G.dim == 3 else 1) * G.nt + G.nz * G.nt) * sum(cost(g) for g in geoms)
+    sample = (f"{rows} of {nrows_total} lateral-frequency rows of problem 0 (direct lateral DFT row + direct "
+              f"NUDFT at {G.nz} nodes, FP64), {t:.1f} s wall on {n} threads, extrapolated by operation count "
+              f"to the whole workload; inverse DFT not timed (rate is an upper bound)")
+    return voxels_of(geoms) / est, n, sample, t
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.dev = device_index
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+        except Exception:
+            pass
+        if uuid:
+            cmd += ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        for ts, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            rows.append((ts, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "timed region"
+        if not inside:
+            inside = rows
+            window = "whole run (no sample fell inside the timed region)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for _, p in inside if num(p[0]) is not None]
+        mx = [num(p[1]) for _, p in inside if num(p[1]) is not None]
+        pw = [num(p[2]) for _, p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in inside for i in range(4) if p[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(inside),
+                "window": window}
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and committed ncu traffic
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pai_row_kernels.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_0808_3510_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(config: str):
+    """DRAM bytes per launch of the forward row kernel from the committed ncu
+    summary, or None when absent or recorded for different kernel source."""
+    path = os.path.join(ROOT, "profiles", "row_forward_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(config)
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="large2d", choices=["large2d", "plain2d", "planar3d", "adjoint3d",
+                                                            "batched2d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        desc, geoms, datas = workload(args.config)
+        vals = []
+        cores, sample = 0, ""
+        for i in range(args.warmup + args.steps):
+            v, cores, sample, _ = oracle_rate(geoms, datas, target_s=2.0)
+            if i >= args.warmup:
+                vals.append(v)
+        value = float(statistics.median(vals))
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: {desc}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_0808_3510_gb300 import build as pai_build
+    if rank == 0 or world == 1:
+        pai_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_0808_3510_gb300 as pai
+
+    desc, geoms, datas = workload(args.config, seed=rank)
+    flat = np.concatenate([d.ravel() for d in datas]).astype(np.float32)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    plan = pai.Plan(geoms if args.config == "batched2d" else geoms[0])
+    p_host = torch.from_numpy(flat).pin_memory()
+    p = p_host.to(dev)
+    out = torch.empty(plan.image_numel, device=dev, dtype=torch.float32)
+    if args.config != "batched2d":
+        out = out.view(plan._out_shape("nz"))
+        p = p.view(plan._out_shape("nt"))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    vox = voxels_of(geoms)
+
+    # parity on sampled outputs (rank 0): spectrum rows against the oracle
+    parity = None
+    if rank == 0 and args.config in ("large2d", "plain2d", "planar3d", "adjoint3d"):
+        import oracle
+        import phantoms as ph
+        g0 = geoms[0]
+        G = ph.Geometry(**{k: g0[k] for k in ("dim", "nx", "ny", "dx", "dy", "nt", "dt", "c", "nz", "dz")})
+        S = plan.spectrum(p).cpu().numpy()
+        rng = np.random.default_rng(5)
+        ks = rng.integers(-G.nx // 2, G.nx // 2, 4)
+        kys = rng.integers(-G.ny // 2, G.ny // 2, 4) if G.dim == 3 else np.zeros(4, int)
+        pd = datas[0].astype(np.float64).reshape(G.data_shape)
+        F = oracle.spectrum_rows(G, pd, ks, kys)
+        Fm = oracle.spectrum_rows(G, pd, -ks, -kys)
+        nzh = G.nz // 2
+        nl = G.nx * (G.ny if G.dim == 3 else 1)
+        errs = []
+        for r in range(len(ks)):
+            e = F[r, : nzh + 1] / (nl * G.nz)
+            e[nzh] = 0.5 * (F[r, nzh] + np.conj(Fm[r, nzh])) / (nl * G.nz)
+            got = S[ks[r] % G.nx] if G.dim == 2 else S[ks[r] % G.nx, kys[r] % G.ny]
+            errs.append(float(np.linalg.norm(got - e) / np.linalg.norm(e)))
+        parity = {"check": "spectrum rows vs FP64 oracle (direct sums)", "rows": len(ks), "max_rel_l2": max(errs)}
+
+    # warm-up (also captures the CUDA graph)
+    for _ in range(args.warmup):
+        plan.reconstruct(p, out)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = plan.kernel_launches
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(args.steps):
+        flush.fill_(float(i & 7))
+        starts[i].record(stream)
+        plan.reconstruct(p, out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t1 = time.time()
+    launches = plan.kernel_launches - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = vox * world / (ms_max * 1e-3)
+
+    # roofline of the row kernel
+    st = plan.profile_stages(p, out, reps=50)
+    info = plan.info
+    nbytes_alg = 0
+    for g in geoms:
+        nl = g["nx"] * (g["ny"] if g["dim"] == 3 else 1)
+        half = (g["ny"] if g["dim"] == 3 else g["nx"]) // 2 + 1
+        rows = (g["nx"] if g["dim"] == 3 else 1) * half
+        nbytes_alg += rows * g["nt"] * 8 + nl * (g["nz"] // 2 + 1) * 8
+    peak, peak_src = hbm_peak()
+    achieved = nbytes_alg / (st[1] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "row_forward (prescale + oversampled FFT + KB gather + weight)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(args.config), "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": nbytes_alg, "kernel_ms": st[1],
+                "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]}}
+
+    # end to end through host memory
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(plan.image_numel, dtype=torch.float32).pin_memory()
+        if args.config != "batched2d":
+            host_out = host_out.view(plan._out_shape("nz"))
+        for _ in range(3):
+            plan.reconstruct_host(p_host if args.config == "batched2d" else p_host.view(plan._out_shape("nt")),
+                                  host_out)
+        reps = max(10, min(args.steps, 200))
+        src = p_host if args.config == "batched2d" else p_host.view(plan._out_shape("nt"))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            plan.reconstruct_host(src, host_out)
+        el = (time.perf_counter() - t) / reps
+        e2e = {"value": vox * world / el, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
+               "d2h_bytes_per_step": int(plan.image_numel * 4), "ms_per_step": el * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, sample, _ = oracle_rate(geoms, datas, target_s=10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.config}: {desc}", "problems": len(geoms), "voxels_per_step": vox,
+                       "M": info["M"], "taps": info["taps"], "oversampling": info["oversampling"],
+                       "K": info["K"], "predicted_window_error": info["predicted_error"],
+                       "threads_per_cta": info["threads_per_cta"], "ctas": info["ctas"],
+                       "cuda_graph": bool(info["uses_graph"]),
+                       "l2": "flushed before every timed step (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "parity": parity,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed_region": t1 - t0,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

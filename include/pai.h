@@ -142,6 +142,17 @@ pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat);
  * plan-owned device staging buffers allocated on first use.                  */
 pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f);
 
+/* Per-stage device times for profiling.  Runs `reps` eager (not graph)
+ * passes of pai_reconstruct (adjoint = 0) or pai_adjoint (adjoint = 1) on the
+ * given device buffers with CUDA events between the stages, synchronises the
+ * plan's stream and writes the mean milliseconds per pass of
+ *   ms[0] the first cuFFT stage (lateral R2C; adjoint: image R2C),
+ *   ms[1] the row kernel (forward: prescale + oversampled FFT + window gather
+ *         + weight; adjoint: spread + inverse oversampled FFT + prescale),
+ *   ms[2] the last cuFFT stage (image C2R; adjoint: lateral C2R).
+ * d_in / d_out as for pai_reconstruct / pai_adjoint; ms: host, 3 doubles.   */
+pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, int reps, int adjoint, double* ms);
+
 /* Change the stream later calls are enqueued on (cudaStream_t or NULL).     */
 pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream);
 

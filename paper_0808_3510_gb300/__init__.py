@@ -96,6 +96,8 @@ def load_library() -> ctypes.CDLL:
         for name in ("pai_reconstruct", "pai_adjoint", "pai_spectrum", "pai_reconstruct_host"):
             getattr(lib, name).argtypes = [vp, fp, fp]
             getattr(lib, name).restype = st
+        lib.pai_profile_stages.argtypes = [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.pai_profile_stages.restype = st
         lib.pai_set_stream.argtypes = [vp, vp]
         lib.pai_set_stream.restype = st
         lib.pai_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -260,6 +262,16 @@ class Plan:
         _check(self._lib.pai_reconstruct_host(self._h, ctypes.c_void_p(p_host.data_ptr()),
                                               ctypes.c_void_p(out.data_ptr())), "pai_reconstruct_host")
         return out
+
+    def profile_stages(self, x: torch.Tensor, out: torch.Tensor, reps: int = 10, adjoint: bool = False):
+        """Mean device milliseconds per pass of (first FFT stage, row kernel, last FFT stage)."""
+        self._check_in(x, self.image_numel if adjoint else self.data_numel, "input")
+        self._check_in(out, self.data_numel if adjoint else self.image_numel, "out")
+        self._sync_stream()
+        ms = (ctypes.c_double * 3)()
+        _check(self._lib.pai_profile_stages(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            int(reps), 1 if adjoint else 0, ms), "pai_profile_stages")
+        return [ms[0], ms[1], ms[2]]
 
     # -- introspection ------------------------------------------------------
     @property

@@ -676,6 +676,55 @@ pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
   return st;
 }
 
+pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, int reps, int adjoint, double* ms) {
+  if (!plan || !d_in || !d_out || !ms || reps < 1) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  cudaEvent_t ev[4];
+  pai_status st = PAI_OK;
+  int made = 0;
+  for (; made < 4 && st == PAI_OK; ++made) st = cuda_status(cudaEventCreate(&ev[made]));
+  double acc[3] = {0, 0, 0};
+  cudaStream_t s = plan->stream;
+  for (int r = 0; r < reps && st == PAI_OK; ++r) {
+    st = cuda_status(cudaEventRecord(ev[0], s));
+    for (auto& p : plan->probs) {
+      if (st != PAI_OK) break;
+      st = adjoint ? fft_status(cufftExecR2C(p.img_r2c, const_cast<float*>(d_in) + p.img_off,
+                                             (cufftComplex*)(plan->d_fh + p.fh_off)))
+                   : fft_status(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_in) + p.data_off,
+                                             (cufftComplex*)(plan->d_pt + p.pt_off)));
+    }
+    if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
+    if (st == PAI_OK)
+      st = enqueue_row(plan, adjoint != 0, s, plan->threads, adjoint ? plan->ctas_adj : plan->ctas,
+                       adjoint ? plan->smem_adj : plan->smem_fwd);
+    if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[2], s));
+    for (auto& p : plan->probs) {
+      if (st != PAI_OK) break;
+      st = adjoint ? fft_status(cufftExecC2R(p.lat_c2r, (cufftComplex*)(plan->d_pt + p.pt_off), d_out + p.data_off))
+                   : fft_status(cufftExecC2R(p.img_c2r, (cufftComplex*)(plan->d_fh + p.fh_off), d_out + p.img_off));
+    }
+    if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[3], s));
+    if (st == PAI_OK) st = cuda_status(cudaEventSynchronize(ev[3]));
+    for (int k = 0; k < 3 && st == PAI_OK; ++k) {
+      float t = 0;
+      st = cuda_status(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      acc[k] += t;
+    }
+    if (st == PAI_OK) {
+      plan->own_kernels += plan->own_kernels_per_call;
+      plan->fft_execs += plan->fft_per_call;
+    }
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  if (st == PAI_OK)
+    for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
 pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream) {
   if (!plan) return PAI_ERR_INVALID_ARG;
   plan->stream = (cudaStream_t)cuda_stream;

@@ -75,10 +75,14 @@ def test_autograd_gradient_is_adjoint_of_residual(pai):
     assert rel(to_np(p.grad), to_np(expect)) < 1e-6
 
 
-def test_finite_differences(pai):
-    """Central differences with step 1e-3 at 32 random coordinates; the loss is
-    evaluated in FP64 from FP32 reconstructions as <a-b, (a+b)/2> - <a-b, f>."""
-    import torch
+@pytest.mark.parametrize("step,tol", [(1e-3, 5e-2), (1.0, 1e-4)])
+def test_finite_differences(pai, step, tol):
+    """Central differences at 32 random coordinates of p for the loss
+    0.5 ||R p - f||^2, evaluated in FP64 from FP32 reconstructions as
+    <a-b, (a+b)/2 - f>.  The loss is quadratic, so the central difference is
+    exact at any step and only FP32 rounding separates it from the gradient:
+    with step 1e-3 that rounding noise (~1e-7 of |R p| divided by the step)
+    is a few percent, with step 1 it is ~1e-5."""
     g = ph.Geometry(dim=3, nx=24, ny=24, nt=48, nz=24)
     plan = pai.Plan(gdict(g, K=3))
     p0 = ph.random_data(72, g).astype(np.float32)
@@ -89,7 +93,6 @@ def test_finite_differences(pai):
     grad = to_np(pt.grad).ravel()
     rng = np.random.default_rng(0)
     idx = rng.choice(p0.size, 32, replace=False)
-    step = 1e-3
     fd = []
     for i in idx:
         a = p0.ravel().copy()
@@ -99,6 +102,6 @@ def test_finite_differences(pai):
         ra = to_np(plan.reconstruct(to_gpu(a.reshape(g.data_shape)))).ravel()
         rb = to_np(plan.reconstruct(to_gpu(b.reshape(g.data_shape)))).ravel()
         d = ra - rb
-        fd.append((np.dot(d, 0.5 * (ra + rb)) - np.dot(d, f_true.ravel())) / (2 * step))
+        fd.append(np.dot(d, 0.5 * (ra + rb) - f_true.ravel()) / (2 * step))
     fd = np.array(fd)
-    assert rel(fd, grad[idx]) < 1e-3
+    assert rel(fd, grad[idx]) < tol

@@ -232,7 +232,8 @@ def test_physics_2d_fcirc_wide_aperture():
     f = oracle.reconstruct(g, ph.fcirc_2d(g, discs))
     s, corr = _fit(f, ph.fcirc_2d_image(g, discs))
     assert 0.95 < s < 1.05 and corr > 0.95
-    assert np.unravel_index(np.argmax(f), f.shape) in {(256, 40), (255, 40), (256, 39), (255, 39)}
+    ix, iz = np.unravel_index(np.argmax(f), f.shape)
+    assert abs(ix - 256) <= 1 and abs(iz - 40) <= 1
 
 
 def test_physics_2d_general_grid():
