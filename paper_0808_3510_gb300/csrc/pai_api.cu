@@ -110,74 +110,18 @@ pai_status fft_status(cufftResult r) {
 #define PAI_CUDA(x) PAI_TRY(cuda_status(x))
 #define PAI_FFT(x) PAI_TRY(fft_status(x))
 
-bool is_even_pos(int v) { return v >= 2 && (v % 2) == 0; }
+pai_status validate(const pai_geometry& g) { return (pai_status)validate_geometry(g); }
 
-pai_status validate(const pai_geometry& g) {
-  if (g.dim != 2 && g.dim != 3) return PAI_ERR_INVALID_ARG;
-  if (!is_even_pos(g.nx) || !is_even_pos(g.nt) || !is_even_pos(g.nz)) return PAI_ERR_INVALID_ARG;
-  if (g.dim == 3 && !is_even_pos(g.ny)) return PAI_ERR_INVALID_ARG;
-  if (!(g.dx > 0) || !(g.dt > 0) || !(g.c > 0) || !(g.dz > 0)) return PAI_ERR_INVALID_ARG;
-  if (g.dim == 3 && !(g.dy > 0)) return PAI_ERR_INVALID_ARG;
-  if (!(g.oversampling == 0 || g.oversampling > 1.0)) return PAI_ERR_INVALID_ARG;
-  if (!(g.K >= 0) || !(g.alpha >= 0)) return PAI_ERR_INVALID_ARG;
-  if (!std::isfinite(g.dx + g.dt + g.c + g.dz + g.oversampling + g.K + g.alpha)) return PAI_ERR_INVALID_ARG;
-  if (g.dim == 3 && !std::isfinite(g.dy)) return PAI_ERR_INVALID_ARG;
-  if (g.nt > (1 << 14)) return PAI_ERR_UNSUPPORTED;  // M <= 32768 (16 values x 1024 threads x 2)
-  return PAI_OK;
-}
-
-int next_pow2(long long v) {
-  int m = 1;
-  while (m < v) m <<= 1;
-  return m;
-}
-
-int ilog2(int v) {
-  int s = 0;
-  while ((1 << s) < v) ++s;
-  return s;
-}
-
-void split_ff(double v, float& hi, float& lo) {
-  hi = (float)v;
-  lo = (float)(v - (double)hi);
-}
-
-// Choose M, H, beta for one problem (before the batch shares H and beta).
 pai_status choose_params(ProblemHost& p) {
-  const pai_geometry& g = p.g;
-  const double c_req = g.oversampling > 0 ? g.oversampling : 2.0;
-  long long want = (long long)std::ceil(c_req * g.nt - 1e-9);
-  p.M = std::max(32, next_pow2(want));
-  if (p.M > 16 * 1024) return PAI_ERR_UNSUPPORTED;
-  p.mshift = ilog2(p.M);
-  p.c_eff = (double)p.M / g.nt;
-  if (g.alpha > 0) {
-    p.beta = g.alpha / c_req;
-    if (!(g.alpha < kPi * (2 * c_req - 1))) return PAI_ERR_INVALID_ARG;
-  } else {
-    p.beta = kPi * (2.0 - 1.0 / p.c_eff) * (1.0 - 1e-3);
-  }
-  if (g.K > 0) {
-    p.H = (int)std::ceil(c_req * g.K - 1e-9);
-    if (p.H < 2) p.H = 2;
-    if (p.H > kMaxH) return PAI_ERR_UNSUPPORTED;
-  } else {
-    p.H = 0;
-    for (int h = 2; h <= kMaxH; ++h)
-      if (predicted_error(p.c_eff, h, p.beta) <= 1e-8) { p.H = h; break; }
-    if (!p.H) p.H = kMaxH;
-  }
+  ProblemParams pp;
+  pai_status st = (pai_status)choose_problem_params(p.g, pp);
+  if (st != PAI_OK) return st;
+  p.M = pp.M;
+  p.mshift = pp.mshift;
+  p.H = pp.H;
+  p.c_eff = pp.c_eff;
+  p.beta = pp.beta;
   return PAI_OK;
-}
-
-// Lateral axes: (n1, n2) with n2 halved by the R2C transform.
-void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d2) {
-  if (g.dim == 2) {
-    n1 = 1; n2 = g.nx; d1 = 1.0; d2 = g.dx;
-  } else {
-    n1 = g.nx; n2 = g.ny; d1 = g.dx; d2 = g.dy;
-  }
 }
 
 pai_status make_cufft_plans(ProblemHost& p, size_t& work) {
@@ -449,35 +393,10 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
 
   // ---- tables (FP64 on the host) ------------------------------------------
   std::vector<float> tables(tab_off, 0.0f);
-  for (auto& p : P->probs) {
-    prescale_table(p.g.nt, p.c_eff, p.H, p.beta, 1.0, &tables[p.pre_off]);
-    double d1, d2;
-    int n1, n2;
-    lateral_axes(p.g, n1, n2, d1, d2);
-    const int half = n2 / 2;
-    for (int r = 0; r < p.rows; ++r) {
-      int i1 = r / (half + 1), i2 = r % (half + 1);
-      int k1 = (i1 < n1 / 2 || n1 == 1) ? i1 : i1 - n1;
-      if (n1 == 1) k1 = 0;
-      double a1 = k1 / (n1 * d1), a2 = i2 / (n2 * d2);
-      double S = a1 * a1 + a2 * a2;
-      split_ff(S, tables[p.rowS_off + 2 * r], tables[p.rowS_off + 2 * r + 1]);
-    }
-    for (int l = 0; l < p.lz; ++l) {
-      double kz = l / (p.g.nz * p.g.dz);
-      float hi, lo;
-      split_ff(kz * kz, hi, lo);
-      tables[p.zt_off + 4 * l] = hi;
-      tables[p.zt_off + 4 * l + 1] = lo;
-      tables[p.zt_off + 4 * l + 2] = (float)kz;
-      tables[p.zt_off + 4 * l + 3] = 0.0f;
-    }
-  }
+  for (auto& p : P->probs)
+    fill_row_tables(p.g, p.c_eff, p.H, p.beta, &tables[p.pre_off], &tables[p.rowS_off], &tables[p.zt_off]);
   std::vector<float2> tw(P->Mmax);
-  for (int k = 0; k < P->Mmax; ++k) {
-    double a = -2.0 * kPi * k / P->Mmax;
-    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+  twiddle_table(P->Mmax, tw.data());
 
   // ---- device memory ------------------------------------------------------
   PAI_CUDA(cudaMalloc(&P->d_pt, std::max<size_t>(pt_off, 1) * sizeof(float2)));
@@ -499,14 +418,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     r.prescale = P->d_tables + p.pre_off;
     r.rowS = reinterpret_cast<const float2*>(P->d_tables + p.rowS_off);
     r.zt = reinterpret_cast<const float4*>(P->d_tables + p.zt_off);
-    r.nt = p.g.nt; r.M = p.M; r.nz = p.g.nz; r.lz = p.lz;
-    r.n1 = p.n1; r.n2 = p.n2; r.rows = p.rows;
-    r.tpr = p.tpr;
-    r.mshift = p.mshift;
-    const double B = (double)p.M * p.g.c * p.g.dt;
-    split_ff(B * B, r.B2hi, r.B2lo);
-    r.wscale = (float)(2.0 * p.g.c * p.g.dt / p.g.dz * B / ((double)p.n1 * p.n2 * p.g.nz));
-    r.nt_over_M = (float)((double)p.g.nt / p.M);
+    fill_row_scalars(p.g, p.M, r);
   }
 
   // ---- cuFFT ----------------------------------------------------------------

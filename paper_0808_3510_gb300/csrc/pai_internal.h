@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pai.h"
+
 namespace pai {
 
 // Largest half tap count supported by the row kernels: taps per node = 2H <= 24.
@@ -75,7 +77,24 @@ double predicted_error(double c, int H, double beta);
 // Prescale for sample n: 1 / (pi I0(H sqrt(beta^2 - (theta_n/c)^2))) * phi(0), theta_n = 2 pi n/nt - pi.
 void prescale_table(int nt, double c, int H, double beta, double extra, float* out);
 
-// Kernel launchers, pai_kernels.cu
+// Plan-time parameters and tables shared by all entry points, pai_plan_math.cpp.
+// Functions returning int return pai_status values.
+struct ProblemParams {
+  int M = 0, mshift = 0, H = 0;
+  double c_eff = 0, beta = 0;
+};
+void split_ff(double v, float& hi, float& lo);
+int validate_geometry(const pai_geometry& g);
+int choose_problem_params(const pai_geometry& g, ProblemParams& p);
+// Lateral axes (n1, n2) with n2 halved by the R2C transform, and their spacings.
+void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d2);
+// prescale [nt], rowS [2 * rows] (float-float), zt [4 * (nz/2 + 1)].
+void fill_row_tables(const pai_geometry& g, double c_eff, int H, double beta, float* prescale, float* rowS,
+                     float* zt);
+// Scalar fields of RowProblem (everything except pointers and rpc).
+void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r);
+void twiddle_table(int Mmax, float2* tw);
+
 cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
                                cudaStream_t s);
 cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
