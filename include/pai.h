@@ -181,6 +181,35 @@ pai_status pai_destroy(pai_plan_t plan);
 pai_status pai_window_probe(int H, double beta, double c, int n, const double* y, double* phi_out,
                             double* pred_err, double* fit_err);
 
+/* Size of the static device scratch array used by pai_spectrum_rows_noalloc. */
+#define PAI_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+/* The fused row stage of pai_spectrum (prescale, oversampled FFT, window
+ * gather and weight for every lateral-frequency row) for ONE problem, with no
+ * device allocation at all.  The paper has no counterpart: this entry point
+ * exists for callers that may not call cudaMalloc / cudaFree (code running
+ * inside another framework's stream capture, processes whose device memory is
+ * already reserved by another allocator or pool, real-time loops in which an
+ * allocation's implicit synchronisation is not allowed).
+ * g:      problem statement, as for pai_plan (host, read during the call).
+ * d_pt:   device, interleaved complex64 lateral spectrum rows [rows][nt], the
+ *         output of an unnormalised real-to-complex FFT of p over the lateral
+ *         axes with the last lateral axis halved: rows = nx/2+1 (2-D) or
+ *         nx*(ny/2+1) (3-D).  Read only.
+ * d_fhat: device, interleaved complex64 [nx][ny][nz/2+1], overwritten with the
+ *         same half spectrum pai_spectrum returns.
+ * cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * Scratch: every table, descriptor and the work counter live in one static
+ * device array of PAI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
+ * library holds until exit; geometries whose tables exceed it return
+ * PAI_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Each call copies its tables from host memory into the array (this waits for
+ * the stream's earlier work) and zeroes the work counter; the array keeps the
+ * last call's contents, and calls that overlap on the GPU race on it.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.              */
+pai_status pai_spectrum_rows_noalloc(const pai_geometry* g, const float* d_pt, float* d_fhat, void* cuda_stream);
+
 /* Static description of a status code; never NULL.                           */
 const char* pai_status_string(pai_status s);
 

@@ -110,6 +110,8 @@ def load_library() -> ctypes.CDLL:
         lib.pai_window_probe.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp,
                                          dp]
         lib.pai_window_probe.restype = st
+        lib.pai_spectrum_rows_noalloc.argtypes = [G, fp, fp, vp]
+        lib.pai_spectrum_rows_noalloc.restype = st
         lib.pai_status_string.argtypes = [st]
         lib.pai_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -153,6 +155,27 @@ def window_probe(H: int, beta: float, c: float, y=()):
     pe, fe = ctypes.c_double(), ctypes.c_double()
     _check(lib.pai_window_probe(H, beta, c, n, ya, out, ctypes.byref(pe), ctypes.byref(fe)), "pai_window_probe")
     return [out[i] for i in range(n)], pe.value, fe.value
+
+
+def spectrum_rows_noalloc(g, pt: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """Fused row stage for callers that cannot allocate device memory
+    (``pai_spectrum_rows_noalloc``).  ``pt``: complex64 lateral spectrum rows
+    (an unnormalised real-to-complex FFT of the data over the lateral axes),
+    ``out``: complex64 half image spectrum, both on the current device and
+    contiguous; runs on torch's current stream and allocates nothing."""
+    lib = load_library()
+    gg = geometry(g)
+    for t in (pt, out):
+        if t.device.type != "cuda" or t.dtype != torch.complex64 or not t.is_contiguous():
+            raise ValueError("pt and out must be contiguous complex64 CUDA tensors")
+    rows = (gg.nx // 2 + 1) if gg.dim == 2 else gg.nx * (gg.ny // 2 + 1)
+    if pt.numel() != rows * gg.nt or out.numel() != _numel(gg, gg.nz // 2 + 1):
+        raise ValueError("pt / out have the wrong number of elements for this geometry")
+    _check(lib.pai_spectrum_rows_noalloc(ctypes.byref(gg), ctypes.c_void_p(pt.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "pai_spectrum_rows_noalloc")
+    return out
 
 
 class Plan:
