@@ -40,6 +40,7 @@ struct ProblemHost {
   size_t pre_off = 0, rowS_off = 0, zt_off = 0;
   cufftHandle lat_r2c = 0, lat_c2r = 0, img_c2r = 0, img_r2c = 0;
   bool have_plans = false;
+  bool own_lateral = false;  // lateral R2C by the library's own kernel (2-D, power-of-two nx)
   size_t data_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nt; }
   size_t img_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nz; }
 };
@@ -58,7 +59,8 @@ struct pai_plan_s {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   std::vector<ProblemHost> probs;
-  int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0;
+  int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
+  int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
   size_t smem_fwd = 0, smem_adj = 0;
   WindowPoly poly{};
   double beta = 0, pred_err = 0, fit_err = 0;
@@ -219,8 +221,9 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.nitems = adjoint ? P->nitems_adj : P->nitems_fwd;
   L.counter = P->d_counter + (adjoint ? 1 : 0);
   L.tw = P->d_tw;
-  L.Mmax = P->Mmax;
+  L.Mmax = P->TW;
   L.H = P->H;
+  L.fft_region = P->fft_region;
   return L;
 }
 
@@ -233,9 +236,16 @@ pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads,
 }
 
 // Stages (a)-(c) for the forward operator, enqueued on s.
+// Stage (a): lateral R2C of problem p, by the library's kernel when it applies, else cuFFT.
+pai_status enqueue_lateral(pai_plan_s* P, const ProblemHost& p, const float* d_p, cudaStream_t s) {
+  if (p.own_lateral)
+    return cuda_status(launch_lateral_r2c(d_p + p.data_off, P->d_pt + p.pt_off, p.g.nx, p.g.nt, P->d_tw,
+                                          P->TW / p.g.nx, s));
+  return fft_status(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_p) + p.data_off, (cufftComplex*)(P->d_pt + p.pt_off)));
+}
+
 pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStream_t s, bool spectrum_only) {
-  for (auto& p : P->probs)
-    PAI_FFT(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_p) + p.data_off, (cufftComplex*)(P->d_pt + p.pt_off)));
+  for (auto& p : P->probs) PAI_TRY(enqueue_lateral(P, p, d_p, s));
   PAI_TRY(enqueue_row(P, false, s, P->threads, P->ctas, P->smem_fwd));
   if (!spectrum_only)
     for (auto& p : P->probs)
@@ -395,19 +405,24 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   std::vector<float> tables(tab_off, 0.0f);
   for (auto& p : P->probs)
     fill_row_tables(p.g, p.c_eff, p.H, p.beta, &tables[p.pre_off], &tables[p.rowS_off], &tables[p.zt_off]);
-  std::vector<float2> tw(P->Mmax);
-  twiddle_table(P->Mmax, tw.data());
+  P->TW = P->Mmax;
+  for (auto& p : P->probs) {
+    p.own_lateral = p.g.dim == 2 && lateral_supported(p.g.nx, p.g.nt);
+    if (p.own_lateral) P->TW = std::max(P->TW, p.g.nx);
+  }
+  std::vector<float2> tw(P->TW);
+  twiddle_table(P->TW, tw.data());
 
   // ---- device memory ------------------------------------------------------
   PAI_CUDA(cudaMalloc(&P->d_pt, std::max<size_t>(pt_off, 1) * sizeof(float2)));
   PAI_CUDA(cudaMalloc(&P->d_fh, std::max<size_t>(fh_off, 1) * sizeof(float2)));
   PAI_CUDA(cudaMalloc(&P->d_tables, std::max<size_t>(tab_off, 4) * sizeof(float)));
-  PAI_CUDA(cudaMalloc(&P->d_tw, P->Mmax * sizeof(float2)));
+  PAI_CUDA(cudaMalloc(&P->d_tw, P->TW * sizeof(float2)));
   PAI_CUDA(cudaMalloc(&P->d_problems, count * sizeof(RowProblem)));
   PAI_CUDA(cudaMalloc(&P->d_counter, 4 * sizeof(int)));
   PAI_CUDA(cudaMemcpy(P->d_tables, tables.data(), tab_off * sizeof(float), cudaMemcpyHostToDevice));
-  PAI_CUDA(cudaMemcpy(P->d_tw, tw.data(), P->Mmax * sizeof(float2), cudaMemcpyHostToDevice));
-  P->ws_bytes = (pt_off + fh_off + P->Mmax) * sizeof(float2) + tab_off * sizeof(float);
+  PAI_CUDA(cudaMemcpy(P->d_tw, tw.data(), P->TW * sizeof(float2), cudaMemcpyHostToDevice));
+  P->ws_bytes = (pt_off + fh_off + P->TW) * sizeof(float2) + tab_off * sizeof(float);
 
   std::vector<RowProblem> rp(count);
   for (int i = 0; i < count; ++i) {
@@ -461,8 +476,11 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     int node_cap = 0;
     for (int i = 0; i < count; ++i) node_cap = std::max(node_cap, rp[i].rpc * (P->probs[i].g.nz + 2));
     P->threads = T;
-    P->smem_fwd = row_smem_forward(T);
-    P->smem_adj = row_smem_forward(T) + (size_t)node_cap * sizeof(float4);
+    size_t region = 0;
+    for (int i = 0; i < count; ++i) region = std::max(region, row_fft_region_bytes(T, P->probs[i].M));
+    P->fft_region = (int)(region / sizeof(float2));
+    P->smem_fwd = region;
+    P->smem_adj = region + (size_t)node_cap * sizeof(float4);
     if (P->smem_fwd > (size_t)smem_optin || P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
     int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H);
     int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H);
@@ -517,8 +535,10 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     if (st != PAI_OK) return st;
   }
   P->ws_bytes += (size_t)P->nitems_fwd * sizeof(WorkItem);
-  P->own_kernels_per_call = 1;       // the row kernel (plus one memset node)
-  P->fft_per_call = 2 * count;
+  int own_lat = 0;
+  for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
+  P->own_kernels_per_call = 1 + own_lat;  // the row kernel and the library's lateral kernels
+  P->fft_per_call = 2 * count - own_lat;
   PAI_CUDA(cudaDeviceSynchronize());
   guard.p = nullptr;
   *out = P;
@@ -605,8 +625,7 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
       if (st != PAI_OK) break;
       st = adjoint ? fft_status(cufftExecR2C(p.img_r2c, const_cast<float*>(d_in) + p.img_off,
                                              (cufftComplex*)(plan->d_fh + p.fh_off)))
-                   : fft_status(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_in) + p.data_off,
-                                             (cufftComplex*)(plan->d_pt + p.pt_off)));
+                   : enqueue_lateral(plan, p, d_in, s);
     }
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
     if (st == PAI_OK)

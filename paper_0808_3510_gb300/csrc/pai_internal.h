@@ -44,6 +44,7 @@ struct RowProblem {
   int n1, n2, rows;
   int tpr;                 // threads per row in the FFT = M / kElemsPerThread
   int rpc;                 // rows per CTA work item
+  int slot;                // complex values per row slot in shared memory (row_slot_stride(M))
   float B2hi, B2lo;        // (M c dt)^2 as float-float: node x = B sqrt(S + az)
   float wscale;            // 2 c dt/dz * B / (n1 n2 nz): W = wscale * kz / x
   float nt_over_M;         // for the node phase
@@ -63,7 +64,12 @@ struct RowLaunch {
   const float2* tw;            // e^{-2 pi i k / Mmax}, k < Mmax
   int Mmax;
   int H;                       // half tap count (taps = 2H)
+  int fft_region;              // complex values of shared memory used by the row slots (adjoint: nodes follow)
 };
+
+// Complex values one row slot needs: the padded FFT layout (one pad per 32)
+// and the flat layout with 2*kMaxH ghost cells must both fit.
+__host__ __device__ inline int row_slot_stride(int M) { return M + ((M >> 5) > 2 * kMaxH ? (M >> 5) : 2 * kMaxH); }
 
 // Host-side window math (FP64), pai_window.cpp
 double bessel_i0(double x);
@@ -99,8 +105,13 @@ cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int thre
                                cudaStream_t s);
 cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
                                cudaStream_t s);
-size_t row_smem_forward(int threads);
-size_t row_smem_adjoint(int threads, int max_nodes_per_row, int rpc_max);
+// Shared memory (bytes) of the row slots of one CTA of `threads` threads for padded length M.
+size_t row_fft_region_bytes(int threads, int M);
+
+// Lateral real-to-complex FFT along x for 2-D problems with power-of-two nx, pai_lateral.cu.
+bool lateral_supported(int nx, int nt);
+cudaError_t launch_lateral_r2c(const float* p, float2* pt, int nx, int nt, const float2* tw, int twstride,
+                               cudaStream_t s);
 int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H);
 
 }  // namespace pai

@@ -12,12 +12,9 @@ PAI_UNIT(5)
 PAI_UNIT(7)
 PAI_UNIT(9)
 
-size_t row_smem_forward(int threads) {
-  return (size_t)threads * kElemsPerThread * 33 / 32 * sizeof(float2);
-}
-
-size_t row_smem_adjoint(int threads, int max_nodes_per_row, int rpc_max) {
-  return row_smem_forward(threads) + (size_t)rpc_max * (size_t)(max_nodes_per_row) * sizeof(float4);
+size_t row_fft_region_bytes(int threads, int M) {
+  const int tpr = M / kElemsPerThread;
+  return (size_t)(threads / tpr) * (size_t)row_slot_stride(M) * sizeof(float2);
 }
 
 cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,

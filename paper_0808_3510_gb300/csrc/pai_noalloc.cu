@@ -132,7 +132,8 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   L.tw = reinterpret_cast<const float2*>(base + o_tw);
   L.Mmax = pp.M;
   L.H = pp.H;
-  const size_t smem = row_smem_forward(threads);
+  const size_t smem = row_fft_region_bytes(threads, pp.M);
+  L.fft_region = (int)(smem / sizeof(float2));
   const int occ = row_kernel_max_ctas_per_sm(false, threads, smem, pp.H);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAI_ERR_CUDA;

@@ -121,6 +121,7 @@ void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r) {
   r.n2 = n2;
   r.rows = n1 * (n2 / 2 + 1);
   r.tpr = M / kElemsPerThread;
+  r.slot = row_slot_stride(M);
   r.mshift = 0;
   while ((1 << r.mshift) < M) ++r.mshift;
   const double B = (double)M * g.c * g.dt;

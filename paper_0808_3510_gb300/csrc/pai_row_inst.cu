@@ -27,8 +27,7 @@ static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, i
                          cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(row_adjoint_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int fft_floats = (int)(row_smem_forward(threads) / sizeof(float));
-  row_adjoint_kernel<H><<<ctas, threads, smem, s>>>(L, w, fft_floats);
+  row_adjoint_kernel<H><<<ctas, threads, smem, s>>>(L, w);
   return cudaGetLastError();
 }
 

@@ -120,17 +120,84 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   for (int i = 0; i < R; ++i) v[i] = a[i];
 }
 
-// One in-place Stockham pass of radix R over X[0..M) (padded indexing).
-// Butterfly j (0 <= j < M/R) reads X[j + r M/R], twiddles by
-// e^{-+2 pi i r (j mod Ns) / (Ns R)}, and writes the R outputs to
-// X[(j - j mod Ns) R + (j mod Ns) + r Ns].  All reads of the pass complete
-// (barrier) before any write.
+// Layouts of a row slot in shared memory.  Passes between the first and the
+// last keep one padding element every 32 (PADI) so strided butterfly accesses
+// do not collide in the banks.  The last pass of the forward transform writes
+// the spectrum unpadded and repeats its first 2*kMaxH values after index M
+// ("ghost cells"), so a node's 2H consecutive taps are plain consecutive
+// addresses even when the window wraps around the period M.
+enum : int { kLayoutPadded = 0, kLayoutFlat = 1, kLayoutFlatGhost = 2 };
+
+// One in-place Stockham pass of radix R.  Butterfly j (0 <= j < M/R) reads
+// X[j + r M/R], twiddles by e^{-+2 pi i r (j mod Ns) / (Ns R)}, and writes its
+// R outputs to X[(j - j mod Ns) R + (j mod Ns) + r Ns].  All reads of the
+// pass complete (barrier) before any write.  OUT selects the write layout.
+// Twiddle powers w^1 .. w^(R-1) from the table entries w^1, w^2, w^4, w^8
+// (loaded before the pass barrier); the others are products of at most
+// three of them, so each power carries at most three extra roundings.
+template <int R>
+struct TwBase {
+  float2 b[R >= 16 ? 4 : R >= 8 ? 3 : R >= 4 ? 2 : 1];
+};
+
+template <int R>
+__device__ __forceinline__ void tw_load(TwBase<R>& t, const float2* __restrict__ tw, int step) {
+  t.b[0] = __ldg(&tw[step]);
+  if (R >= 4) t.b[1] = __ldg(&tw[2 * step]);
+  if (R >= 8) t.b[2] = __ldg(&tw[4 * step]);
+  if (R >= 16) t.b[3] = __ldg(&tw[8 * step]);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 twc(float2 w) {
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
+// v[r] *= w^r for r = 1..R-1, each power formed right before its use so only
+// the base entries stay live.
 template <int R, bool INV>
+__device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
+  const float2 w1 = t.b[0];
+  v[1] = cmul(v[1], twc<INV>(w1));
+  if (R >= 4) {
+    const float2 w2 = t.b[1];
+    const float2 w3 = cmul(w1, w2);
+    v[2] = cmul(v[2], twc<INV>(w2));
+    v[3] = cmul(v[3], twc<INV>(w3));
+    if (R >= 8) {
+      const float2 w4 = t.b[2];
+      const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+      v[4] = cmul(v[4], twc<INV>(w4));
+      v[5] = cmul(v[5], twc<INV>(w5));
+      v[6] = cmul(v[6], twc<INV>(w6));
+      v[7] = cmul(v[7], twc<INV>(w7));
+      if (R >= 16) {
+        const float2 w8 = t.b[3];
+        v[8] = cmul(v[8], twc<INV>(w8));
+        v[9] = cmul(v[9], twc<INV>(cmul(w1, w8)));
+        v[10] = cmul(v[10], twc<INV>(cmul(w2, w8)));
+        v[11] = cmul(v[11], twc<INV>(cmul(w3, w8)));
+        v[12] = cmul(v[12], twc<INV>(cmul(w4, w8)));
+        v[13] = cmul(v[13], twc<INV>(cmul(w5, w8)));
+        v[14] = cmul(v[14], twc<INV>(cmul(w6, w8)));
+        v[15] = cmul(v[15], twc<INV>(cmul(w7, w8)));
+      }
+    }
+  }
+}
+
+template <int R, bool INV, int OUT>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
                                          int twstride) {
   constexpr int NB = kElemsPerThread / R;
   float2 v[NB][R];
+  TwBase<R> t[NB];
   const int MR = M / R;
+  const int tws = (M / (Ns * R)) * twstride;
+  // twiddles do not depend on the data: for radix 16 (one butterfly per
+  // thread) their loads are issued before the barrier; smaller radices carry
+  // several butterflies per thread and load after it to stay within registers
+  if (Ns > 1 && NB == 1) tw_load<R>(t[0], tw, (lane & (Ns - 1)) * tws);
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int j = lane + i * tpr;
@@ -141,45 +208,90 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
     }
   }
   __syncthreads();
-  const int tws = (M / (Ns * R)) * twstride;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int j = lane + i * tpr;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = k * tws;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * step]);
-        if (INV) w.y = -w.y;
-        v[i][r] = cmul(v[i][r], w);
-      }
+      if (NB != 1) tw_load<R>(t[i], tw, k * tws);
+      tw_apply<R, INV>(v[i], t[i]);
     }
     dft_reg<R, INV>(v[i]);
     const int base = (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int idx = base + r * Ns;
-      X[PADI(idx)] = v[i][r];
+      if (OUT == kLayoutPadded) {
+        X[PADI(idx)] = v[i][r];
+      } else {
+        X[idx] = v[i][r];
+        if (OUT == kLayoutFlatGhost && idx < 2 * kMaxH) X[M + idx] = v[i][r];
+      }
     }
   }
   __syncthreads();
 }
 
-// Length-M FFT (M = 2^mshift >= 32) of each row slot's X, in shared memory.
-template <bool INV>
-__device__ __forceinline__ void fft_smem(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
+// First forward pass (radix 16, Ns = 1) fed straight from global memory:
+// position m = j + r M/16 of the oversampled input holds sample
+// n = m + nt/2 (mod M) times the prescale when n < nt, else zero (Algorithm 1
+// prescale and zero padding, centred so that the e^{+i pi j/c} part of the
+// Proposition's phase is absorbed).  Writes padded.
+__device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int nt, int lane, int tpr,
+                                                           const float2* __restrict__ src,
+                                                           const float* __restrict__ prescale) {
+  constexpr int R = 16;
+  float2 v[R];
+  const int MR = M / R, mask = M - 1, h = nt >> 1;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int m = lane + r * MR;
+    const int n = (m + h) & mask;
+    float2 a = make_float2(0.f, 0.f);
+    if (n < nt) {
+      const float2 g = __ldg(&src[n]);
+      const float s = __ldg(&prescale[n]);
+      a = make_float2(s * g.x, s * g.y);
+    }
+    v[r] = a;
+  }
+  dft_reg<R, false>(v);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int idx = lane * R + r;
+    X[PADI(idx)] = v[r];
+  }
+  __syncthreads();
+}
+
+// Remaining passes after a first radix-16 pass (Ns = 16 on entry); the last
+// pass writes layout OUT.
+template <bool INV, int OUT>
+__device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
                                          int twstride) {
-  int Ns = 1;
-  int rem = mshift;
-  while (rem >= 4) {
-    fft_pass<16, INV>(X, M, Ns, lane, tpr, tw, twstride);
+  int Ns = 16;
+  int rem = mshift - 4;
+  while (rem > 4 || rem == 4) {
+    if (rem == 4) {
+      fft_pass<16, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+      return;
+    }
+    fft_pass<16, INV, kLayoutPadded>(X, M, Ns, lane, tpr, tw, twstride);
     Ns <<= 4;
     rem -= 4;
   }
-  if (rem == 3) fft_pass<8, INV>(X, M, Ns, lane, tpr, tw, twstride);
-  else if (rem == 2) fft_pass<4, INV>(X, M, Ns, lane, tpr, tw, twstride);
-  else if (rem == 1) fft_pass<2, INV>(X, M, Ns, lane, tpr, tw, twstride);
+  if (rem == 3) fft_pass<8, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+  else if (rem == 2) fft_pass<4, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+  else if (rem == 1) fft_pass<2, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+}
+
+// Length-M FFT (M = 2^mshift >= 32) of a padded row slot, in shared memory;
+// the last pass writes layout OUT.
+template <bool INV, int OUT>
+__device__ __forceinline__ void fft_smem(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
+                                         int twstride) {
+  fft_pass<16, INV, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
+  fft_rest<INV, OUT>(X, M, mshift, lane, tpr, tw, twstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -231,12 +343,24 @@ __device__ __forceinline__ void negate_node(int j0p, float frp, int& j0, float& 
   }
 }
 
-// e^{+i pi nu} for nu = (j0 + fr) nt / M, returned as (cos, sin)
+// e^{+i pi nu} for nu = (j0 + fr) nt / M, returned as (cos, sin).
+// The integer part is reduced exactly: pi j0 nt / M modulo 2 pi is
+// pi m2 / M with m2 = j0 nt mod 2M.  When M = 2 nt that angle is a multiple of
+// pi/2 and becomes an exact quarter-turn rotation.
 __device__ __forceinline__ float2 node_phase(int j0, float fr, int nt, int M, float nt_over_M) {
-  const int m2 = (int)(((long long)j0 * (long long)nt) & (2LL * M - 1));
-  float s1, c1, s2, c2;
-  sincospif((float)m2 / (float)M, &s1, &c1);
+  float s2, c2;
   sincospif(fr * nt_over_M, &s2, &c2);
+  if (M == 2 * nt) {
+    switch (j0 & 3) {
+      case 0: return make_float2(c2, s2);
+      case 1: return make_float2(-s2, c2);
+      case 2: return make_float2(-c2, -s2);
+      default: return make_float2(s2, -c2);
+    }
+  }
+  const int m2 = (int)(((long long)j0 * (long long)nt) & (2LL * M - 1));
+  float s1, c1;
+  sincospif((float)m2 / (float)M, &s1, &c1);
   return make_float2(c1 * c2 - s1 * s2, s1 * c2 + c1 * s2);
 }
 
@@ -257,21 +381,30 @@ __device__ __forceinline__ void tap_weights(const WindowPoly& W, float fr, float
   }
 }
 
-// P(nu) = e^{-i pi nu} sum_t w_t G[(j0 + t) mod M], t = -H+1..H   (Eq. nufft-a)
+// P(nu) = e^{-i pi nu} sum_t w_t G[(j0 + t) mod M], t = -H+1..H   (Eq. nufft-a).
+// U is the flat spectrum with ghost cells: the 2H taps are U[b .. b+2H-1],
+// b = (j0 - H + 1) mod M.  Weights are formed pair by pair (tap it and its
+// mirror 2H-1-it) and consumed at once.
 template <int H>
-__device__ __forceinline__ float2 node_value(const float2* X, const WindowPoly& W, int j0, float fr, int M, int nt,
+__device__ __forceinline__ float2 node_value(const float2* U, const WindowPoly& W, int j0, float fr, int M, int nt,
                                              float nt_over_M) {
-  float w[2 * H];
-  tap_weights<H>(W, fr, w);
-  const int mask = M - 1;
-  const int base = (j0 - H + 1) & mask;
+  const float2* g = U + ((j0 - H + 1) & (M - 1));
+  const float z = fr - 0.5f, z2 = z * z;
   float ax = 0.0f, ay = 0.0f;
 #pragma unroll
-  for (int it = 0; it < 2 * H; ++it) {
-    const int idx = (base + it) & mask;
-    const float2 g = X[PADI(idx)];
-    ax = fmaf(w[it], g.x, ax);
-    ay = fmaf(w[it], g.y, ay);
+  for (int p = 0; p < H; ++p) {
+    float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+    for (int e = kHalfCoef - 2; e >= 0; --e) {
+      E = fmaf(E, z2, W.ce[p][e]);
+      O = fmaf(O, z2, W.co[p][e]);
+    }
+    const float wl = fmaf(z, O, E), wh = fmaf(-z, O, E);
+    const float2 gl = g[p], gh = g[2 * H - 1 - p];
+    ax = fmaf(wl, gl.x, ax);
+    ay = fmaf(wl, gl.y, ay);
+    ax = fmaf(wh, gh.x, ax);
+    ay = fmaf(wh, gh.y, ay);
   }
   const float2 ph = node_phase(j0, fr, nt, M, nt_over_M);
   return make_float2(fmaf(ax, ph.x, ay * ph.y), fmaf(ay, ph.x, -ax * ph.y));
@@ -368,26 +501,15 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     if (item >= L.nitems) break;
     const WorkItem wi = L.items[item];
     const RowProblem& P = L.problems[wi.problem];
-    const int tpr = P.tpr, M = P.M, nt = P.nt;
+    const int tpr = P.tpr, M = P.M;
     const int slot = threadIdx.x / tpr;
     const int lane = threadIdx.x - slot * tpr;
     const int row = wi.row0 + slot;
     const bool valid = row < P.rows;
-    float2* X = smem + slot * (M + (M >> 5));
-    if (valid) {
-      // prescale + centre: sample n goes to position n - nt/2 (mod M)
-      const float2* src = P.pt + (size_t)row * nt;
-      const int mask = M - 1, h = nt >> 1;
-      for (int n = lane; n < nt; n += tpr) {
-        const float2 v = __ldg(&src[n]);
-        const float s = __ldg(&P.prescale[n]);
-        const int m = (n - h) & mask;
-        X[PADI(m)] = make_float2(s * v.x, s * v.y);
-      }
-      for (int m = h + lane; m < M - h; m += tpr) X[PADI(m)] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    fft_smem<false>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
+    float2* X = smem + slot * P.slot;
+    // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
+    fft_first_pass_from_global(X, M, P.nt, lane, tpr, P.pt + (size_t)(valid ? row : 0) * P.nt, P.prescale);
+    fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
     if (valid) gather_row<H>(P, W, X, row, lane);
   }
 }
@@ -417,7 +539,7 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
 }
 
 template <int H>
-__global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPoly W, int fft_floats) {
+__global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
   __shared__ float sce[kHalfCoef * kMaxH], sco[kHalfCoef * kMaxH];
@@ -426,7 +548,7 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     sce[i] = W.ce[p][e];
     sco[i] = W.co[p][e];
   }
-  float4* nodes_all = reinterpret_cast<float4*>(smem + fft_floats / 2);
+  float4* nodes_all = reinterpret_cast<float4*>(smem + L.fft_region);
   for (;;) {
     const int item = next_item(L.counter, &s_item);
     if (item >= L.nitems) break;
@@ -437,7 +559,7 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     const int lane = threadIdx.x - slot * tpr;
     const int row = wi.row0 + slot;
     const bool valid = row < P.rows;
-    float2* X = smem + slot * (M + (M >> 5));
+    float2* X = smem + slot * P.slot;
     float4* N = nodes_all + slot * (P.nz + 2);
     const int nzh = P.nz >> 1;
     RowGeom rg;
@@ -527,13 +649,13 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
       for (int q = 0; q < kElemsPerThread; ++q) X[PADI(a + q)] = acc[q];
     }
     __syncthreads();
-    fft_smem<true>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
+    fft_smem<true, kLayoutFlat>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
     if (valid) {
       const float scale = rg.mirror ? 0.5f : 1.0f;
       float2* dst = const_cast<float2*>(P.pt) + (size_t)row * nt;
       const int h = nt >> 1;
       for (int n = lane; n < nt; n += tpr) {
-        const float2 v = X[PADI((n - h) & mask)];
+        const float2 v = X[(n - h) & mask];
         const float s = scale * __ldg(&P.prescale[n]);
         dst[n] = make_float2(s * v.x, s * v.y);
       }
