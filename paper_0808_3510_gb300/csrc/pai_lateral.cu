@@ -30,15 +30,19 @@ __global__ void __launch_bounds__(1024) lateral_r2c_kernel(const float* __restri
   const int T = blockDim.x;
   // load the tile: thread t takes column pair f = t % FP of detectors x = t / FP + i T / FP
   {
+    // T / FP = nx / 16 threads per column pair, so each thread loads exactly
+    // kElemsPerThread detectors: issue all loads before the shared stores
     const int f = threadIdx.x % FP;
     const int x0 = threadIdx.x / FP;
     const int xs = T / FP;
-    const int ncol = nt - n0;  // columns left (>= 2, even)
-    for (int x = x0; x < nx; x += xs) {
-      float2 z = make_float2(0.f, 0.f);
-      if (2 * f < ncol) z = __ldg(reinterpret_cast<const float2*>(p + (size_t)x * nt + n0) + f);
-      smem[f * S + PADI(x)] = z;
-    }
+    const bool live = 2 * f < nt - n0;  // columns left (>= 2, even)
+    const float2* src = reinterpret_cast<const float2*>(p + (size_t)x0 * nt + n0) + f;
+    float2 z[kElemsPerThread];
+#pragma unroll
+    for (int i = 0; i < kElemsPerThread; ++i)
+      z[i] = live ? __ldg(src + (size_t)i * xs * (nt / 2)) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kElemsPerThread; ++i) smem[f * S + PADI(x0 + i * xs)] = z[i];
   }
   __syncthreads();
   {

@@ -351,12 +351,15 @@ __device__ __forceinline__ float2 node_phase(int j0, float fr, int nt, int M, fl
   float s2, c2;
   sincospif(fr * nt_over_M, &s2, &c2);
   if (M == 2 * nt) {
-    switch (j0 & 3) {
-      case 0: return make_float2(c2, s2);
-      case 1: return make_float2(-s2, c2);
-      case 2: return make_float2(-c2, -s2);
-      default: return make_float2(s2, -c2);
+    // multiply (c2, s2) by i^(j0 mod 4) with selects, no divergent branch
+    const int q = j0 & 3;
+    float a = (q & 1) ? -s2 : c2;
+    float b = (q & 1) ? c2 : s2;
+    if (q & 2) {
+      a = -a;
+      b = -b;
     }
+    return make_float2(a, b);
   }
   const int m2 = (int)(((long long)j0 * (long long)nt) & (2LL * M - 1));
   float s1, c1;
@@ -456,11 +459,23 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
     out1[0] = make_float2(0.f, 0.f);
     if (rg.mirror) out2[0] = make_float2(0.f, 0.f);
   }
+  // the depth-table entry of the next node is loaded one iteration ahead
+  int lp_next = 0;
+  {
+    bool n_, y_;
+    if (lane < nA) node_task(lane, nzh, nA, lp_next, n_, y_);
+  }
+  float4 zt_next = __ldg(&P.zt[lp_next]);
   for (int i = lane; i < nA; i += P.tpr) {
     int lp;
     bool neg, nyq;
     node_task(i, nzh, nA, lp, neg, nyq);
-    const float4 zt = __ldg(&P.zt[lp]);
+    const float4 zt = zt_next;
+    if (i + P.tpr < nA) {
+      bool n_, y_;
+      node_task(i + P.tpr, nzh, nA, lp_next, n_, y_);
+      zt_next = __ldg(&P.zt[lp_next]);
+    }
     int j0p, j0;
     float frp, fr, x0;
     node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
