@@ -64,7 +64,7 @@ class PlanInfo(ctypes.Structure):
         ("oversampling", ctypes.c_double), ("K", ctypes.c_double), ("alpha", ctypes.c_double),
         ("predicted_error", ctypes.c_double), ("threads_per_cta", ctypes.c_int), ("ctas", ctypes.c_int),
         ("rows", ctypes.c_int), ("nodes", ctypes.c_longlong), ("workspace_bytes", ctypes.c_size_t),
-        ("uses_graph", ctypes.c_int),
+        ("uses_graph", ctypes.c_int), ("library_ffts", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -61,6 +61,7 @@ struct pai_plan_s {
   std::vector<ProblemHost> probs;
   int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
+  bool zf = false;  // every stage by the library's kernels: lateral FFTs + depth-fused row kernels
   size_t smem_fwd = 0, smem_adj = 0;
   WindowPoly poly{};
   double beta = 0, pred_err = 0, fit_err = 0;
@@ -227,38 +228,81 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   return L;
 }
 
-pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads, int ctas, size_t smem) {
+pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads, int ctas, size_t smem,
+                       bool zf = false) {
   RowLaunch L = make_launch(P, adjoint);
   PAI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(int), s));
-  cudaError_t e = adjoint ? launch_row_adjoint(L, P->poly, threads, ctas, smem, s)
-                          : launch_row_forward(L, P->poly, threads, ctas, smem, s);
+  cudaError_t e = adjoint ? launch_row_adjoint(L, P->poly, threads, ctas, smem, s, zf)
+                          : launch_row_forward(L, P->poly, threads, ctas, smem, s, zf);
   return cuda_status(e);
 }
 
-// Stages (a)-(c) for the forward operator, enqueued on s.
-// Stage (a): lateral R2C of problem p, by the library's kernel when it applies, else cuFFT.
+// Lateral forward transform (Eq. fft-1a) of a real array x[x][(y)][c], c < C,
+// into complex rows out[row][c] (row = i1 (n2/2+1) + i2), by the library's
+// kernels: 2-D one R2C along x; 3-D an R2C along y then an in-place C2C
+// along x.  The adjoint uses the same transform on the image (C = nz).
+pai_status own_lateral_fwd(pai_plan_s* P, const ProblemHost& p, const float* in, float2* out, int C, cudaStream_t s) {
+  const pai_geometry& g = p.g;
+  if (g.dim == 2) return cuda_status(launch_lateral_r2c(in, out, g.nx, C, 1, P->d_tw, P->TW / g.nx, s));
+  PAI_CUDA(launch_lateral_r2c(in, out, g.ny, C, g.nx, P->d_tw, P->TW / g.ny, s));
+  return cuda_status(launch_lateral_c2c(out, out, g.nx, (g.ny / 2 + 1) * C, 1, false, P->d_tw, P->TW / g.nx, s));
+}
+
+// Lateral inverse (Hermitian C2R) of complex rows in[row][c] into the real
+// array out[x][(y)][c]; 3-D runs the C2C along x in place on `in` first.
+pai_status own_lateral_inv(pai_plan_s* P, const ProblemHost& p, float2* in, float* out, int C, cudaStream_t s) {
+  const pai_geometry& g = p.g;
+  if (g.dim == 2) return cuda_status(launch_lateral_c2r(in, out, g.nx, C, 1, P->d_tw, P->TW / g.nx, s));
+  PAI_CUDA(launch_lateral_c2c(in, in, g.nx, (g.ny / 2 + 1) * C, 1, true, P->d_tw, P->TW / g.nx, s));
+  return cuda_status(launch_lateral_c2r(in, out, g.ny, C, g.nx, P->d_tw, P->TW / g.ny, s));
+}
+
+// Stage (a) of the forward operator for problem p.
 pai_status enqueue_lateral(pai_plan_s* P, const ProblemHost& p, const float* d_p, cudaStream_t s) {
-  if (p.own_lateral)
-    return cuda_status(launch_lateral_r2c(d_p + p.data_off, P->d_pt + p.pt_off, p.g.nx, p.g.nt, P->d_tw,
-                                          P->TW / p.g.nx, s));
+  if (P->zf || p.own_lateral) return own_lateral_fwd(P, p, d_p + p.data_off, P->d_pt + p.pt_off, p.g.nt, s);
   return fft_status(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_p) + p.data_off, (cufftComplex*)(P->d_pt + p.pt_off)));
 }
 
+// Stage (c) of the forward operator for problem p: depth-row layout -> inverse
+// depth FFT of every row, then the lateral C2R.
+pai_status enqueue_inverse(pai_plan_s* P, const ProblemHost& p, float* d_f, cudaStream_t s) {
+  if (P->zf) {
+    PAI_CUDA(launch_rows_c2c(P->d_fh + p.fh_off, p.g.nz, p.rows, true, P->d_tw, P->TW / p.g.nz, s));
+    return own_lateral_inv(P, p, P->d_fh + p.fh_off, d_f + p.img_off, p.g.nz, s);
+  }
+  return fft_status(cufftExecC2R(p.img_c2r, (cufftComplex*)(P->d_fh + p.fh_off), d_f + p.img_off));
+}
+
+// First and last stages of the adjoint for problem p.
+pai_status enqueue_adj_first(pai_plan_s* P, const ProblemHost& p, const float* d_h, cudaStream_t s) {
+  if (P->zf) {
+    PAI_TRY(own_lateral_fwd(P, p, d_h + p.img_off, P->d_fh + p.fh_off, p.g.nz, s));
+    return cuda_status(launch_rows_c2c(P->d_fh + p.fh_off, p.g.nz, p.rows, false, P->d_tw, P->TW / p.g.nz, s));
+  }
+  return fft_status(cufftExecR2C(p.img_r2c, const_cast<float*>(d_h) + p.img_off, (cufftComplex*)(P->d_fh + p.fh_off)));
+}
+
+pai_status enqueue_adj_last(pai_plan_s* P, const ProblemHost& p, float* d_pbar, cudaStream_t s) {
+  if (P->zf) return own_lateral_inv(P, p, P->d_pt + p.pt_off, d_pbar + p.data_off, p.g.nt, s);
+  return fft_status(cufftExecC2R(p.lat_c2r, (cufftComplex*)(P->d_pt + p.pt_off), d_pbar + p.data_off));
+}
+
+// Stages (a)-(c) for the forward operator, enqueued on s.  spectrum_only
+// stops after the row stage with the half image spectrum in d_fh (always the
+// non-fused row kernel).
 pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStream_t s, bool spectrum_only) {
   for (auto& p : P->probs) PAI_TRY(enqueue_lateral(P, p, d_p, s));
-  PAI_TRY(enqueue_row(P, false, s, P->threads, P->ctas, P->smem_fwd));
+  const bool zf = P->zf && !spectrum_only;
+  PAI_TRY(enqueue_row(P, false, s, P->threads, P->ctas, P->smem_fwd, zf));
   if (!spectrum_only)
-    for (auto& p : P->probs)
-      PAI_FFT(cufftExecC2R(p.img_c2r, (cufftComplex*)(P->d_fh + p.fh_off), d_f + p.img_off));
+    for (auto& p : P->probs) PAI_TRY(enqueue_inverse(P, p, d_f, s));
   return PAI_OK;
 }
 
 pai_status enqueue_adjoint(pai_plan_s* P, const float* d_h, float* d_pbar, cudaStream_t s) {
-  for (auto& p : P->probs)
-    PAI_FFT(cufftExecR2C(p.img_r2c, const_cast<float*>(d_h) + p.img_off, (cufftComplex*)(P->d_fh + p.fh_off)));
-  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj));
-  for (auto& p : P->probs)
-    PAI_FFT(cufftExecC2R(p.lat_c2r, (cufftComplex*)(P->d_pt + p.pt_off), d_pbar + p.data_off));
+  for (auto& p : P->probs) PAI_TRY(enqueue_adj_first(P, p, d_h, s));
+  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj, P->zf));
+  for (auto& p : P->probs) PAI_TRY(enqueue_adj_last(P, p, d_pbar, s));
   return PAI_OK;
 }
 
@@ -369,6 +413,26 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // row slots of a CTA must tile it exactly: the CTA size is a power of two
   if (threads > 1024 || (threads & (threads - 1)) != 0) return PAI_ERR_UNSUPPORTED;
 
+  // ---- pipeline: all stages by the library's kernels when every size allows -----
+  {
+    const char* env_zf = std::getenv("PAI_FUSED_DEPTH");
+    bool zf = !(env_zf && env_zf[0] == '0');
+    for (auto& p : P->probs) {
+      const pai_geometry& g = p.g;
+      const bool nz_ok = (g.nz & (g.nz - 1)) == 0 && g.nz >= 32 && g.nz <= 16384;
+      bool lat_ok;
+      if (g.dim == 2) {
+        lat_ok = lateral_supported(g.nx, g.nt) && lateral_supported(g.nx, g.nz);
+      } else {
+        const int h = g.ny / 2 + 1;
+        lat_ok = lateral_supported(g.ny, g.nt) && lateral_supported(g.ny, g.nz) &&
+                 lateral_supported(g.nx, h * g.nt) && lateral_supported(g.nx, h * g.nz);
+      }
+      zf = zf && nz_ok && lat_ok;
+    }
+    P->zf = zf;
+  }
+
   // ---- layout -------------------------------------------------------------
   size_t data_off = 0, img_off = 0, pt_off = 0, fh_off = 0, tab_off = 0;
   auto align4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
@@ -385,7 +449,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     data_off += p.data_len();
     img_off += p.img_len();
     pt_off += (size_t)p.rows * p.g.nt;
-    fh_off += (size_t)p.n1 * p.n2 * p.lz;
+    // half image spectrum [n1 n2][lz] (non-fused row kernel) or depth rows [rows][nz] (fused)
+    fh_off += std::max((size_t)p.n1 * p.n2 * p.lz, (size_t)p.rows * p.g.nz);
     p.pre_off = tab_off;
     tab_off = align4(tab_off + p.g.nt);
     p.rowS_off = tab_off;
@@ -408,7 +473,11 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   P->TW = P->Mmax;
   for (auto& p : P->probs) {
     p.own_lateral = p.g.dim == 2 && lateral_supported(p.g.nx, p.g.nt);
-    if (p.own_lateral) P->TW = std::max(P->TW, p.g.nx);
+    if (p.own_lateral || P->zf) P->TW = std::max(P->TW, p.g.nx);
+    if (P->zf) {
+      P->TW = std::max(P->TW, p.g.nz);
+      if (p.g.dim == 3) P->TW = std::max(P->TW, p.g.ny);
+    }
   }
   std::vector<float2> tw(P->TW);
   twiddle_table(P->TW, tw.data());
@@ -477,13 +546,14 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     for (int i = 0; i < count; ++i) node_cap = std::max(node_cap, rp[i].rpc * (P->probs[i].g.nz + 2));
     P->threads = T;
     size_t region = 0;
-    for (int i = 0; i < count; ++i) region = std::max(region, row_fft_region_bytes(T, P->probs[i].M));
+    for (int i = 0; i < count; ++i)
+      region = std::max(region, (size_t)rp[i].rpc * (size_t)rp[i].slot * sizeof(float2));
     P->fft_region = (int)(region / sizeof(float2));
     P->smem_fwd = region;
     P->smem_adj = region + (size_t)node_cap * sizeof(float4);
     if (P->smem_fwd > (size_t)smem_optin || P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
-    int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H);
-    int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H);
+    int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H, P->zf);
+    int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);
     if (occ_f < 1 || occ_a < 1) return PAI_ERR_UNSUPPORTED;
     std::vector<WorkItem> items;
     build_items(T, items);
@@ -514,7 +584,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       float best = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, P->cap_stream);
-        if (enqueue_row(P, false, P->cap_stream, T, P->ctas, P->smem_fwd) != PAI_OK) break;
+        if (enqueue_row(P, false, P->cap_stream, T, P->ctas, P->smem_fwd, P->zf) != PAI_OK) break;
         cudaEventRecord(e1, P->cap_stream);
         cudaEventSynchronize(e1);
         float ms = 0;
@@ -534,11 +604,61 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     for (int T = threads; T >= std::max(tpr_max, 32) && st != PAI_OK; T /= 2) st = finish_shape(T);
     if (st != PAI_OK) return st;
   }
+  // ---- tuner: when both pipelines apply, keep the faster one ----------------
+  // (library kernels for every stage vs cuFFT for the inverse and the adjoint's
+  // image-side and data-side transforms), timed on one eager forward pass each
+  if (P->zf && tune) {
+    float* d_in = nullptr;
+    float* d_out = nullptr;
+    float ms_zf = 1e30f, ms_cufft = 1e30f;
+    if (cudaMalloc(&d_in, P->data_total * sizeof(float)) == cudaSuccess &&
+        cudaMalloc(&d_out, P->img_total * sizeof(float)) == cudaSuccess &&
+        cudaMemset(d_in, 0, P->data_total * sizeof(float)) == cudaSuccess) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int variant = 0; variant < 2; ++variant) {
+        P->zf = variant == 0;
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(e0, P->cap_stream);
+          set_fft_streams(P, P->cap_stream);
+          if (enqueue_forward(P, d_in, d_out, P->cap_stream, false) != PAI_OK) break;
+          cudaEventRecord(e1, P->cap_stream);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) best = std::min(best, ms);
+        }
+        (variant == 0 ? ms_zf : ms_cufft) = best;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      set_fft_streams(P, P->stream);
+    }
+    cudaFree(d_in);
+    cudaFree(d_out);
+    cudaGetLastError();
+    P->zf = ms_zf <= ms_cufft;
+    if (!P->zf) {
+      int own_lat = 0;
+      for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
+      P->own_kernels_per_call = 1 + own_lat;
+      P->fft_per_call = 2 * count - own_lat;
+    }
+  }
   P->ws_bytes += (size_t)P->nitems_fwd * sizeof(WorkItem);
-  int own_lat = 0;
-  for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
-  P->own_kernels_per_call = 1 + own_lat;  // the row kernel and the library's lateral kernels
-  P->fft_per_call = 2 * count - own_lat;
+  if (P->zf) {
+    int k = 1;  // the row kernel
+    for (auto& p : P->probs) k += (p.g.dim == 2) ? 3 : 5;  // lateral forward + depth FFT + lateral inverse
+    P->own_kernels_per_call = k;
+    P->fft_per_call = 0;
+  } else {
+    int own_lat = 0;
+    for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
+    P->own_kernels_per_call = 1 + own_lat;  // the row kernel and the library's lateral kernels
+    P->fft_per_call = 2 * count - own_lat;
+  }
   PAI_CUDA(cudaDeviceSynchronize());
   guard.p = nullptr;
   *out = P;
@@ -576,11 +696,19 @@ pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat) {
   if (prev != plan->device) cudaSetDevice(plan->device);
   pai_status st = enqueue_forward(plan, d_p, nullptr, plan->stream, true);
   if (st == PAI_OK) {
-    size_t n = 0;
-    for (auto& p : plan->probs) n += (size_t)p.n1 * p.n2 * p.lz;
-    st = cuda_status(cudaMemcpyAsync(d_fhat, plan->d_fh, n * sizeof(float2), cudaMemcpyDeviceToDevice, plan->stream));
+    size_t out = 0;
+    for (auto& p : plan->probs) {
+      const size_t n = (size_t)p.n1 * p.n2 * p.lz;
+      if (st == PAI_OK)
+        st = cuda_status(cudaMemcpyAsync(reinterpret_cast<float2*>(d_fhat) + out, plan->d_fh + p.fh_off,
+                                         n * sizeof(float2), cudaMemcpyDeviceToDevice, plan->stream));
+      out += n;
+    }
     plan->own_kernels += 1;
-    plan->fft_execs += (long long)plan->probs.size();
+    for (auto& p : plan->probs) {
+      if (plan->zf || p.own_lateral) plan->own_kernels += (p.g.dim == 2) ? 1 : 2;
+      else plan->fft_execs += 1;
+    }
   }
   if (prev != plan->device) cudaSetDevice(prev);
   return st;
@@ -623,19 +751,16 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
     st = cuda_status(cudaEventRecord(ev[0], s));
     for (auto& p : plan->probs) {
       if (st != PAI_OK) break;
-      st = adjoint ? fft_status(cufftExecR2C(p.img_r2c, const_cast<float*>(d_in) + p.img_off,
-                                             (cufftComplex*)(plan->d_fh + p.fh_off)))
-                   : enqueue_lateral(plan, p, d_in, s);
+      st = adjoint ? enqueue_adj_first(plan, p, d_in, s) : enqueue_lateral(plan, p, d_in, s);
     }
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
     if (st == PAI_OK)
       st = enqueue_row(plan, adjoint != 0, s, plan->threads, adjoint ? plan->ctas_adj : plan->ctas,
-                       adjoint ? plan->smem_adj : plan->smem_fwd);
+                       adjoint ? plan->smem_adj : plan->smem_fwd, plan->zf);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[2], s));
     for (auto& p : plan->probs) {
       if (st != PAI_OK) break;
-      st = adjoint ? fft_status(cufftExecC2R(p.lat_c2r, (cufftComplex*)(plan->d_pt + p.pt_off), d_out + p.data_off))
-                   : fft_status(cufftExecC2R(p.img_c2r, (cufftComplex*)(plan->d_fh + p.fh_off), d_out + p.img_off));
+      st = adjoint ? enqueue_adj_last(plan, p, d_out, s) : enqueue_inverse(plan, p, d_out, s);
     }
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[3], s));
     if (st == PAI_OK) st = cuda_status(cudaEventSynchronize(ev[3]));
@@ -678,6 +803,7 @@ pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info) {
   info->nodes = plan->nodes;
   info->workspace_bytes = plan->ws_bytes;
   info->uses_graph = plan->use_graph ? 1 : 0;
+  info->library_ffts = plan->zf ? 1 : 0;
   return PAI_OK;
 }
 

@@ -49,6 +49,7 @@ struct RowProblem {
   float wscale;            // 2 c dt/dz * B / (n1 n2 nz): W = wscale * kz / x
   float nt_over_M;         // for the node phase
   int mshift;              // log2(M)
+  int nzshift;             // log2(nz) when nz is a power of two, else 0
 };
 
 struct WorkItem {
@@ -101,17 +102,25 @@ void fill_row_tables(const pai_geometry& g, double c_eff, int H, double beta, fl
 void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r);
 void twiddle_table(int Mmax, float2* tw);
 
+// zf selects the depth-fused kernels (see pai_row_kernels.cuh).
 cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                               cudaStream_t s);
+                               cudaStream_t s, bool zf = false);
 cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                               cudaStream_t s);
+                               cudaStream_t s, bool zf = false);
 // Shared memory (bytes) of the row slots of one CTA of `threads` threads for padded length M.
 size_t row_fft_region_bytes(int threads, int M);
 
-// Lateral real-to-complex FFT along x for 2-D problems with power-of-two nx, pai_lateral.cu.
-bool lateral_supported(int nx, int nt);
-cudaError_t launch_lateral_r2c(const float* p, float2* pt, int nx, int nt, const float2* tw, int twstride,
+// FFTs along a strided axis of A[outer][L][C] for power-of-two L, pai_lateral.cu.
+bool lateral_supported(int L, int C);
+cudaError_t launch_lateral_r2c(const float* in, float2* out, int L, int C, int outer, const float2* tw, int twstride,
                                cudaStream_t s);
-int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H);
+cudaError_t launch_lateral_c2r(const float2* in, float* out, int L, int C, int outer, const float2* tw, int twstride,
+                               cudaStream_t s);
+cudaError_t launch_lateral_c2c(const float2* in, float2* out, int L, int C, int outer, bool inverse, const float2* tw,
+                               int twstride, cudaStream_t s);
+// In-place FFT of `rows` contiguous complex lines of power-of-two length L (32 <= L <= 16384).
+cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const float2* tw, int twstride,
+                            cudaStream_t s);
+int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H, bool zf = false);
 
 }  // namespace pai

@@ -4,9 +4,9 @@
 namespace pai {
 
 #define PAI_UNIT(lo)                                                                                          \
-  cudaError_t row_forward_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t);    \
-  cudaError_t row_adjoint_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t);    \
-  int row_occupancy_h##lo(int, bool, int, size_t);
+  cudaError_t row_forward_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t, bool); \
+  cudaError_t row_adjoint_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t, bool); \
+  int row_occupancy_h##lo(int, bool, int, size_t, bool);
 PAI_UNIT(2)
 PAI_UNIT(5)
 PAI_UNIT(7)
@@ -18,28 +18,28 @@ size_t row_fft_region_bytes(int threads, int M) {
 }
 
 cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool zf) {
   const int H = L.H;
-  if (H < 5) return row_forward_h2(H, L, w, threads, ctas, smem, s);
-  if (H < 7) return row_forward_h5(H, L, w, threads, ctas, smem, s);
-  if (H < 9) return row_forward_h7(H, L, w, threads, ctas, smem, s);
-  return row_forward_h9(H, L, w, threads, ctas, smem, s);
+  if (H < 5) return row_forward_h2(H, L, w, threads, ctas, smem, s, zf);
+  if (H < 7) return row_forward_h5(H, L, w, threads, ctas, smem, s, zf);
+  if (H < 9) return row_forward_h7(H, L, w, threads, ctas, smem, s, zf);
+  return row_forward_h9(H, L, w, threads, ctas, smem, s, zf);
 }
 
 cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool zf) {
   const int H = L.H;
-  if (H < 5) return row_adjoint_h2(H, L, w, threads, ctas, smem, s);
-  if (H < 7) return row_adjoint_h5(H, L, w, threads, ctas, smem, s);
-  if (H < 9) return row_adjoint_h7(H, L, w, threads, ctas, smem, s);
-  return row_adjoint_h9(H, L, w, threads, ctas, smem, s);
+  if (H < 5) return row_adjoint_h2(H, L, w, threads, ctas, smem, s, zf);
+  if (H < 7) return row_adjoint_h5(H, L, w, threads, ctas, smem, s, zf);
+  if (H < 9) return row_adjoint_h7(H, L, w, threads, ctas, smem, s, zf);
+  return row_adjoint_h9(H, L, w, threads, ctas, smem, s, zf);
 }
 
-int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H) {
-  if (H < 5) return row_occupancy_h2(H, adjoint, threads, smem);
-  if (H < 7) return row_occupancy_h5(H, adjoint, threads, smem);
-  if (H < 9) return row_occupancy_h7(H, adjoint, threads, smem);
-  return row_occupancy_h9(H, adjoint, threads, smem);
+int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H, bool zf) {
+  if (H < 5) return row_occupancy_h2(H, adjoint, threads, smem, zf);
+  if (H < 7) return row_occupancy_h5(H, adjoint, threads, smem, zf);
+  if (H < 9) return row_occupancy_h7(H, adjoint, threads, smem, zf);
+  return row_occupancy_h9(H, adjoint, threads, smem, zf);
 }
 
 }  // namespace pai

@@ -124,6 +124,9 @@ void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r) {
   r.slot = row_slot_stride(M);
   r.mshift = 0;
   while ((1 << r.mshift) < M) ++r.mshift;
+  r.nzshift = 0;
+  if ((g.nz & (g.nz - 1)) == 0)
+    while ((1 << r.nzshift) < g.nz) ++r.nzshift;
   const double B = (double)M * g.c * g.dt;
   split_ff(B * B, r.B2hi, r.B2lo);
   r.wscale = (float)(2.0 * g.c * g.dt / g.dz * B / ((double)n1 * n2 * g.nz));

@@ -13,41 +13,42 @@
 
 namespace pai {
 
-template <int H>
-static cudaError_t fwd_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                         cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(row_forward_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename K>
+static cudaError_t launch_k(K kernel, const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
+                           cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  row_forward_kernel<H><<<ctas, threads, smem, s>>>(L, w);
+  kernel<<<ctas, threads, smem, s>>>(L, w);
   return cudaGetLastError();
 }
 
-template <int H>
-static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                         cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(row_adjoint_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  row_adjoint_kernel<H><<<ctas, threads, smem, s>>>(L, w);
-  return cudaGetLastError();
-}
-
-template <int H>
-static int occ_h(bool adjoint, int threads, size_t smem) {
+template <typename K>
+static int occ_k(K kernel, int threads, size_t smem) {
   int n = 0;
-  if (adjoint) {
-    if (cudaFuncSetAttribute(row_adjoint_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, row_adjoint_kernel<H>, threads, smem) != cudaSuccess)
-      return 0;
-  } else {
-    if (cudaFuncSetAttribute(row_forward_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, row_forward_kernel<H>, threads, smem) != cudaSuccess)
-      return 0;
-  }
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 0;
   return n;
+}
+
+template <int H>
+static cudaError_t fwd_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem, cudaStream_t s,
+                         bool zf) {
+  return zf ? launch_k(row_forward_kernel<H, true>, L, w, threads, ctas, smem, s)
+            : launch_k(row_forward_kernel<H, false>, L, w, threads, ctas, smem, s);
+}
+
+template <int H>
+static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem, cudaStream_t s,
+                         bool zf) {
+  return zf ? launch_k(row_adjoint_kernel<H, true>, L, w, threads, ctas, smem, s)
+            : launch_k(row_adjoint_kernel<H, false>, L, w, threads, ctas, smem, s);
+}
+
+template <int H>
+static int occ_h(bool adjoint, int threads, size_t smem, bool zf) {
+  if (adjoint)
+    return zf ? occ_k(row_adjoint_kernel<H, true>, threads, smem) : occ_k(row_adjoint_kernel<H, false>, threads, smem);
+  return zf ? occ_k(row_forward_kernel<H, true>, threads, smem) : occ_k(row_forward_kernel<H, false>, threads, smem);
 }
 
 #define PAI_ONE(F, HH, ...) \
@@ -60,19 +61,19 @@ static int occ_h(bool adjoint, int threads, size_t smem) {
 
 // Returns cudaErrorNotSupported when H is outside this unit's range.
 cudaError_t PAI_FN(row_forward)(int H, const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                                cudaStream_t s) {
-  PAI_ALL(fwd_h, L, w, threads, ctas, smem, s)
+                                cudaStream_t s, bool zf) {
+  PAI_ALL(fwd_h, L, w, threads, ctas, smem, s, zf)
   return cudaErrorNotSupported;
 }
 
 cudaError_t PAI_FN(row_adjoint)(int H, const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,
-                                cudaStream_t s) {
-  PAI_ALL(adj_h, L, w, threads, ctas, smem, s)
+                                cudaStream_t s, bool zf) {
+  PAI_ALL(adj_h, L, w, threads, ctas, smem, s, zf)
   return cudaErrorNotSupported;
 }
 
-int PAI_FN(row_occupancy)(int H, bool adjoint, int threads, size_t smem) {
-  PAI_ALL(occ_h, adjoint, threads, smem)
+int PAI_FN(row_occupancy)(int H, bool adjoint, int threads, size_t smem, bool zf) {
+  PAI_ALL(occ_h, adjoint, threads, smem, zf)
   return -1;
 }
 

@@ -188,7 +188,7 @@ __device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
 
 template <int R, bool INV, int OUT>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
-                                         int twstride) {
+                                         int twstride, bool active = true) {
   constexpr int NB = kElemsPerThread / R;
   float2 v[NB][R];
   TwBase<R> t[NB];
@@ -197,19 +197,22 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
   // twiddles do not depend on the data: for radix 16 (one butterfly per
   // thread) their loads are issued before the barrier; smaller radices carry
   // several butterflies per thread and load after it to stay within registers
-  if (Ns > 1 && NB == 1) tw_load<R>(t[0], tw, (lane & (Ns - 1)) * tws);
+  if (active) {
+    if (Ns > 1 && NB == 1) tw_load<R>(t[0], tw, (lane & (Ns - 1)) * tws);
 #pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int j = lane + i * tpr;
+    for (int i = 0; i < NB; ++i) {
+      const int j = lane + i * tpr;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int idx = j + r * MR;
-      v[i][r] = X[PADI(idx)];
+      for (int r = 0; r < R; ++r) {
+        const int idx = j + r * MR;
+        v[i][r] = X[PADI(idx)];
+      }
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
+    if (!active) break;
     const int j = lane + i * tpr;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
@@ -268,30 +271,32 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
 // pass writes layout OUT.
 template <bool INV, int OUT>
 __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
-                                         int twstride) {
+                                         int twstride, bool active = true) {
   int Ns = 16;
   int rem = mshift - 4;
-  while (rem > 4 || rem == 4) {
+  while (rem >= 4) {
     if (rem == 4) {
-      fft_pass<16, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+      fft_pass<16, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
       return;
     }
-    fft_pass<16, INV, kLayoutPadded>(X, M, Ns, lane, tpr, tw, twstride);
+    fft_pass<16, INV, kLayoutPadded>(X, M, Ns, lane, tpr, tw, twstride, active);
     Ns <<= 4;
     rem -= 4;
   }
-  if (rem == 3) fft_pass<8, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
-  else if (rem == 2) fft_pass<4, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
-  else if (rem == 1) fft_pass<2, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride);
+  if (rem == 3) fft_pass<8, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
+  else if (rem == 2) fft_pass<4, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
+  else if (rem == 1) fft_pass<2, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
 }
 
 // Length-M FFT (M = 2^mshift >= 32) of a padded row slot, in shared memory;
 // the last pass writes layout OUT.
+// Threads with active == false take part in the barriers only (used when a
+// shorter transform runs on a row slot sized for a longer one).
 template <bool INV, int OUT>
 __device__ __forceinline__ void fft_smem(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
-                                         int twstride) {
-  fft_pass<16, INV, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
-  fft_rest<INV, OUT>(X, M, mshift, lane, tpr, tw, twstride);
+                                         int twstride, bool active = true) {
+  fft_pass<16, INV, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride, active);
+  fft_rest<INV, OUT>(X, M, mshift, lane, tpr, tw, twstride, active);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,6 +504,56 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
   }
 }
 
+// Depth-row layout: the row's own full depth spectrum F[l], l in
+// [-nz/2, nz/2), stored at Zs[l mod nz] (Zs = the row's line of the output),
+// from the row's nodes at +nu (l > 0) and -nu (l < 0):  F[l] = W P(sign(l)|K|)
+// for 0 < |l| < nz/2, F[0] = 0 (l = 0 rule), F[-nz/2] = W (P(+|K|) + P(-|K|))/2
+// (Nyquist rule).  An inverse depth FFT of each line followed by the lateral
+// C2R completes Eq. (fft-1).
+template <int H>
+__device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPoly& W, const float2* X, float2* Zs,
+                                             int row, int lane) {
+  const float2 S = P.rowS[row];
+  const int nzh = P.nz >> 1;
+  const int nA = P.nz - 1;
+  if (lane == 0) Zs[0] = make_float2(0.f, 0.f);
+  int lp_next = 0;
+  {
+    bool n_, y_;
+    if (lane < nA) node_task(lane, nzh, nA, lp_next, n_, y_);
+  }
+  float4 zt_next = __ldg(&P.zt[lp_next]);
+  for (int i = lane; i < nA; i += P.tpr) {
+    int lp;
+    bool neg, nyq;
+    node_task(i, nzh, nA, lp, neg, nyq);
+    const float4 zt = zt_next;
+    if (i + P.tpr < nA) {
+      bool n_, y_;
+      node_task(i + P.tpr, nzh, nA, lp_next, n_, y_);
+      zt_next = __ldg(&P.zt[lp_next]);
+    }
+    int j0p, j0;
+    float frp, fr, x0;
+    node_position(S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+    const float wt = P.wscale * zt.z / x0;
+    if (!neg) {
+      const float2 v = node_value<H>(X, W, j0p, frp, P.M, P.nt, P.nt_over_M);
+      if (nyq) {
+        negate_node(j0p, frp, j0, fr);
+        const float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+        Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
+      } else {
+        Zs[lp] = make_float2(wt * v.x, wt * v.y);
+      }
+    } else {
+      negate_node(j0p, frp, j0, fr);
+      const float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+      Zs[P.nz - lp] = make_float2(wt * u.x, wt * u.y);
+    }
+  }
+}
+
 // Fetch the next work item for the whole CTA (dynamic scheduling).
 __device__ __forceinline__ int next_item(int* counter, int* s_item) {
   __syncthreads();
@@ -507,7 +562,10 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
   return *s_item;
 }
 
-template <int H>
+// ZF = false: writes the half image spectrum fhat[k][l'] (both lateral
+// destinations k and -k); ZF = true: writes the row's own full depth spectrum
+// F[row][l mod nz] (see gather_row_z).
+template <int H, bool ZF>
 __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
@@ -525,7 +583,10 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
     fft_first_pass_from_global(X, M, P.nt, lane, tpr, P.pt + (size_t)(valid ? row : 0) * P.nt, P.prescale);
     fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
-    if (valid) gather_row<H>(P, W, X, row, lane);
+    if (valid) {
+      if (!ZF) gather_row<H>(P, W, X, row, lane);
+      else gather_row_z<H>(P, W, X, P.fh + (size_t)row * P.nz, row, lane);
+    }
   }
 }
 
@@ -553,7 +614,10 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
 
-template <int H>
+// ZF = false: input is the half image spectrum (image R2C over all axes) with
+// both lateral destinations of a row; ZF = true: input is the row's own full
+// depth spectrum Fbar[row][l mod nz].
+template <int H, bool ZF>
 __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
@@ -579,7 +643,43 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     const int nzh = P.nz >> 1;
     RowGeom rg;
     int nneg = 1, nn = 0;
-    if (valid) {
+    // ZF: the row's depth spectrum Fbar[l mod nz] (depth FFT of the lateral R2C of the image)
+    const float2* Zs = P.fh + (size_t)(valid ? row : 0) * P.nz;
+    if (valid && ZF) {
+      rg.S = P.rowS[row];
+      rg.mirror = true;
+      nneg = nzh;
+      nn = nneg + nzh;
+      const int nA = P.nz - 1;
+      for (int i = lane; i < nA; i += tpr) {
+        int lp;
+        bool neg, nyq;
+        node_task(i, nzh, nA, lp, neg, nyq);
+        const float4 zt = __ldg(&P.zt[lp]);
+        int j0p, j0;
+        float frp, fr, x0;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+        const float wt = P.wscale * zt.z / x0;
+        negate_node(j0p, frp, j0, fr);
+        if (nyq) {
+          const float2 y = Zs[nzh];
+          const float2 pb = make_float2(0.5f * wt * y.x, 0.5f * wt * y.y);
+          const float2 qp = cmul(pb, node_phase(j0p, frp, nt, M, P.nt_over_M));
+          const float2 qn = cmul(pb, node_phase(j0, fr, nt, M, P.nt_over_M));
+          N[nneg + nzh - 1] = make_float4(__int_as_float(j0p), frp, qp.x, qp.y);
+          N[0] = make_float4(__int_as_float(j0), fr, qn.x, qn.y);
+        } else if (!neg) {
+          const float2 y = Zs[lp];
+          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), node_phase(j0p, frp, nt, M, P.nt_over_M));
+          N[nneg + lp - 1] = make_float4(__int_as_float(j0p), frp, q.x, q.y);
+        } else {
+          const float2 y = Zs[P.nz - lp];
+          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), node_phase(j0, fr, nt, M, P.nt_over_M));
+          N[nzh - lp] = make_float4(__int_as_float(j0), fr, q.x, q.y);
+        }
+      }
+    }
+    if (valid && !ZF) {
       rg = row_geom(P, row);
       nneg = rg.mirror ? nzh : 1;
       nn = nneg + nzh;
@@ -666,7 +766,7 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     __syncthreads();
     fft_smem<true, kLayoutFlat>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
     if (valid) {
-      const float scale = rg.mirror ? 0.5f : 1.0f;
+      const float scale = (!ZF && rg.mirror) ? 0.5f : 1.0f;
       float2* dst = const_cast<float2*>(P.pt) + (size_t)row * nt;
       const int h = nt >> 1;
       for (int n = lane; n < nt; n += tpr) {

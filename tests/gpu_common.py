@@ -59,3 +59,19 @@ def oracle_half_spectrum(g, F):
         partner = np.conj(F[nx_][:, ny_, nzh])
     E[..., nzh] = 0.5 * (F[..., nzh] + partner) / (n_lat * g.nz)
     return E
+
+
+# Both pipelines a plan can run: every stage on the library's kernels (chosen
+# when all sizes are powers of two and the tuner is off), or cuFFT for the
+# inverse / adjoint image-side transforms.
+PIPELINES = {
+    "library_ffts": {"PAI_AUTOTUNE": "0", "PAI_FUSED_DEPTH": "1"},
+    "cufft_inverse": {"PAI_FUSED_DEPTH": "0"},
+}
+
+
+@pytest.fixture(params=sorted(PIPELINES))
+def pipeline(request, monkeypatch):
+    for k, v in PIPELINES[request.param].items():
+        monkeypatch.setenv(k, v)
+    return request.param

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import phantoms as ph
-from gpu_common import DOT_TOL, TOL, gdict, pai, rel, to_gpu, to_np  # noqa: F401
+from gpu_common import DOT_TOL, TOL, gdict, pai, pipeline, rel, to_gpu, to_np  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -19,11 +19,13 @@ CASES = [
     ph.Geometry(dim=2, nx=6, nt=10, nz=4),
     ph.Geometry(dim=3, nx=20, ny=12, nt=48, nz=18, dx=0.9, dy=1.1, dt=0.7, c=1.3, dz=1.0),
     ph.Geometry(dim=3, nx=32, ny=32, nt=64, nz=32),
+    ph.Geometry(dim=3, nx=64, ny=32, nt=128, nz=64, dy=1.2),
+    ph.Geometry(dim=2, nx=256, nt=512, nz=256, dz=0.8),
 ]
 
 
 @pytest.mark.parametrize("g", CASES, ids=lambda g: f"{g.dim}d-{g.nx}x{g.ny}x{g.nt}-{g.nz}")
-def test_dot_product_identity(pai, g):
+def test_dot_product_identity(pai, g, pipeline):
     plan = pai.Plan(gdict(g, K=3))
     p = ph.random_data(50, g)
     h = ph.random_image(51, g)
@@ -38,7 +40,7 @@ def test_dot_product_identity(pai, g):
 
 
 @pytest.mark.parametrize("g", CASES, ids=lambda g: f"{g.dim}d-{g.nx}x{g.ny}x{g.nt}-{g.nz}")
-def test_adjoint_against_oracle(pai, g):
+def test_adjoint_against_oracle(pai, g, pipeline):
     plan = pai.Plan(gdict(g, K=3))
     h = ph.random_image(52, g).astype(np.float32)
     got = to_np(plan.adjoint(to_gpu(h)))
@@ -46,7 +48,7 @@ def test_adjoint_against_oracle(pai, g):
     assert rel(got, ref) < TOL
 
 
-def test_adjoint_batched(pai):
+def test_adjoint_batched(pai, pipeline):
     geoms = [ph.Geometry(dim=2, nx=64, nt=130, nz=64), ph.Geometry(dim=2, nx=36, nt=512, nz=100),
              ph.Geometry(dim=3, nx=10, ny=8, nt=40, nz=16)]
     plan = pai.Plan([gdict(g, K=3) for g in geoms])

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import phantoms as ph
-from gpu_common import TOL, gdict, oracle_half_spectrum, pai, rel, to_gpu, to_np  # noqa: F401
+from gpu_common import TOL, gdict, oracle_half_spectrum, pai, pipeline, rel, to_gpu, to_np  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -25,12 +25,13 @@ def _ref(g, p):
     return oracle.reconstruct(g, np.asarray(p, dtype=np.float32).astype(np.float64))
 
 
-def test_plain_2d_128x256(pai):
+def test_plain_2d_128x256(pai, pipeline):
     """2-D line detector, 128 detectors x 256 samples -> 128 x 128 (c = 2, K = 3)."""
     prob = ph.plain_2d(0)
     f, plan = _recon(pai, prob.geom, prob.p, oversampling=2, K=3)
     info = plan.info
     assert info["M"] == 512 and info["taps"] == 12
+    assert info["library_ffts"] == (1 if pipeline == "library_ffts" else 0)
     assert rel(f, _ref(prob.geom, prob.p)) < TOL
 
 
@@ -61,7 +62,7 @@ def test_2d_tiny_and_degenerate(pai, shape):
 
 
 @pytest.mark.parametrize("K,os_", [(4, 2), (3, 3), (2, 2), (1.5, 4)])
-def test_2d_window_parameters(pai, K, os_):
+def test_2d_window_parameters(pai, K, os_, pipeline):
     g = ph.Geometry(dim=2, nx=64, nt=200, nz=96)
     p = ph.random_data(23, g)
     f, plan = _recon(pai, g, p, K=K, oversampling=os_)
@@ -69,14 +70,14 @@ def test_2d_window_parameters(pai, K, os_):
     assert rel(f, _ref(g, p)) < TOL
 
 
-def test_3d_general_grid(pai):
+def test_3d_general_grid(pai, pipeline):
     g = ph.Geometry(dim=3, nx=20, ny=12, nt=48, nz=18, dx=0.9, dy=1.1, dt=0.7, c=1.3, dz=1.0)
     p = ph.random_data(24, g)
     f, _ = _recon(pai, g, p, K=3)
     assert rel(f, _ref(g, p)) < TOL
 
 
-def test_3d_planar_128(pai):
+def test_3d_planar_128(pai, pipeline):
     """3-D planar: 128 x 128 detectors x 256 samples -> 128^3, uniform balls."""
     prob = ph.planar_3d(0)
     f, plan = _recon(pai, prob.geom, prob.p, oversampling=2, K=3)
@@ -142,7 +143,7 @@ def test_bad_tensors_rejected(pai):
         plan.reconstruct(torch.zeros(32, 16, device="cuda").t())
 
 
-def test_batched_uneven_matches_oracle_and_single_plans(pai):
+def test_batched_uneven_matches_oracle_and_single_plans(pai, pipeline):
     import torch
     geoms = [ph.Geometry(dim=2, nx=64, nt=130, nz=64), ph.Geometry(dim=2, nx=36, nt=512, nz=100),
              ph.Geometry(dim=2, nx=128, nt=66, nz=34, dt=0.8), ph.Geometry(dim=3, nx=10, ny=8, nt=40, nz=16)]
@@ -159,7 +160,7 @@ def test_batched_uneven_matches_oracle_and_single_plans(pai):
     assert off == out.size
 
 
-def test_large_2d_sampled_rows(pai):
+def test_large_2d_sampled_rows(pai, pipeline):
     """2-D large (2048 x 4096 -> 2048 x 2048, c = 2, K = 4) in the launch
     configuration the benchmark times: sampled spectrum rows against the
     oracle's row-by-row direct sums, and the image against an FP64 inverse FFT
@@ -182,3 +183,15 @@ def test_large_2d_sampled_rows(pai):
     f = to_np(plan.reconstruct(pt))
     ref = np.fft.irfft2(S.astype(np.complex128) * (g.nx * g.nz), s=(g.nx, g.nz))
     assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 32), (32, 64, 64), (256, 64, 128)])
+def test_3d_power_of_two_both_pipelines(pai, pipeline, shape):
+    """3-D grids whose sizes all are powers of two (the library-FFT pipeline
+    applies: R2C along y, C2C along x, depth FFT, and their inverses)."""
+    n, nt, nz = shape
+    g = ph.Geometry(dim=3, nx=n, ny=max(32, n // 2), nt=nt, nz=nz, dy=1.3, dz=0.9)
+    p = ph.random_data(90, g)
+    f, plan = _recon(pai, g, p, K=3)
+    assert plan.info["library_ffts"] == (1 if pipeline == "library_ffts" else 0)
+    assert rel(f, _ref(g, p)) < TOL
