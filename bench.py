@@ -332,9 +332,27 @@ def main():
             errs.append(float(np.linalg.norm(got - e) / np.linalg.norm(e)))
         parity = {"check": "spectrum rows vs FP64 oracle (direct sums)", "rows": len(ks), "max_rel_l2": max(errs)}
 
-    # warm-up (also captures the CUDA graph)
+    grad_mode = args.config == "adjoint3d"
+    if grad_mode:
+        # one step = the gradient of 0.5 ||R p - f_true||^2 with respect to p
+        import phantoms as ph
+        g0 = geoms[0]
+        G = ph.Geometry(**{k: g0[k] for k in ("dim", "nx", "ny", "dx", "dy", "nt", "dt", "c", "nz", "dz")})
+        prob = ph.adjoint_3d(rank)
+        f_true = torch.from_numpy(ph.balls_3d_image(G, prob.objects).astype(np.float32)).to(dev)
+        grad = torch.empty_like(p)
+
+    def step():
+        if grad_mode:
+            plan.reconstruct(p, out)
+            out.sub_(f_true)
+            plan.adjoint(out, grad)
+        else:
+            plan.reconstruct(p, out)
+
+    # warm-up (also captures the CUDA graphs)
     for _ in range(args.warmup):
-        plan.reconstruct(p, out)
+        step()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(torch.cuda.current_device())
@@ -350,7 +368,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i & 7))
         starts[i].record(stream)
-        plan.reconstruct(p, out)
+        step()
         ends[i].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -370,6 +388,7 @@ def main():
 
     # roofline of the row kernel
     st = plan.profile_stages(p, out, reps=50)
+    st_adj = plan.profile_stages(out, grad, reps=20, adjoint=True) if grad_mode else None
     info = plan.info
     nbytes_alg = 0
     for g in geoms:
@@ -384,6 +403,44 @@ def main():
                 "traffic": recorded_traffic(args.config), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": nbytes_alg, "kernel_ms": st[1],
                 "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]}}
+    if st_adj is not None:
+        roofline["adjoint_stage_ms"] = {"image_fft": st_adj[0], "row_adjoint_kernel": st_adj[1],
+                                        "lateral_inverse_fft": st_adj[2]}
+
+    # batched vs plain: the same problems as separate plans, one after another, no graph
+    batched = None
+    if args.config == "batched2d":
+        os.environ["PAI_USE_GRAPH"] = "0"
+        plans = [pai.Plan(g) for g in geoms]
+        del os.environ["PAI_USE_GRAPH"]
+        ins, outs, off_i, off_o = [], [], 0, 0
+        for g, pl in zip(geoms, plans):
+            ni, no = pl.data_numel, pl.image_numel
+            ins.append(p[off_i: off_i + ni].view(pl._out_shape("nt")))
+            outs.append(out[off_o: off_o + no].view(pl._out_shape("nz")))
+            off_i += ni
+            off_o += no
+        for _ in range(3):
+            for pl, a, o in zip(plans, ins, outs):
+                pl.reconstruct(a, o)
+        torch.cuda.synchronize()
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(float(i & 7))
+            e0.record(stream)
+            for pl, a, o in zip(plans, ins, outs):
+                pl.reconstruct(a, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        plain_ms = tot / reps
+        batched = {"batched_ms_per_step": ms, "plain_ms_per_step": plain_ms,
+                   "plain": f"{len(geoms)} separate plans, sequential, eager (no CUDA graph)",
+                   "speedup": plain_ms / ms}
+        for pl in plans:
+            pl.close()
 
     # end to end through host memory
     e2e = None
@@ -423,6 +480,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "parity": parity,
             "roofline": roofline,
+            "batched_vs_plain": batched,
+            "step": "gradient of 0.5||R p - f||^2 (reconstruct + residual + adjoint)" if grad_mode else "reconstruct",
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -61,6 +61,7 @@ struct pai_plan_s {
   std::vector<ProblemHost> probs;
   int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
+  int chunk = 128, bin_offset = 0, bin_slot = 0;  // adjoint sorted-bin spread
   bool zf = false;  // every stage by the library's kernels: lateral FFTs + depth-fused row kernels
   size_t smem_fwd = 0, smem_adj = 0;
   WindowPoly poly{};
@@ -225,6 +226,9 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.Mmax = P->TW;
   L.H = P->H;
   L.fft_region = P->fft_region;
+  L.chunk = P->chunk;
+  L.bin_offset = P->bin_offset;
+  L.bin_slot = P->bin_slot;
   return L;
 }
 
@@ -550,7 +554,26 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       region = std::max(region, (size_t)rp[i].rpc * (size_t)rp[i].slot * sizeof(float2));
     P->fft_region = (int)(region / sizeof(float2));
     P->smem_fwd = region;
-    P->smem_adj = region + (size_t)node_cap * sizeof(float4);
+    int nz_max = 0, rpc_max = 0;
+    for (int i = 0; i < count; ++i) {
+      nz_max = std::max(nz_max, P->probs[i].g.nz);
+      rpc_max = std::max(rpc_max, rp[i].rpc);
+    }
+    // Chunk of the adjoint spread: at most the threads of a row slot (one node
+    // per thread) and spanning fewer than M - 2H cells (same-sign nodes are at
+    // most M c dt / (nz dz) cells apart).
+    double gap = 1.0;
+    int tpr_min = 1 << 30, m_min = 1 << 30;
+    for (auto& p : P->probs) {
+      gap = std::max(gap, (double)p.M * p.g.c * p.g.dt / (p.g.nz * p.g.dz));
+      tpr_min = std::min(tpr_min, p.tpr);
+      m_min = std::min(m_min, p.M);
+    }
+    const int span_cap = std::max(1, (int)((m_min - 2 * P->H - 1) / (std::ceil(gap) + 1)));
+    P->chunk = std::max(1, std::min(tpr_min, span_cap));
+    P->bin_slot = 0;
+    P->bin_offset = (int)(region + (size_t)node_cap * sizeof(float4));
+    P->smem_adj = (size_t)P->bin_offset;
     if (P->smem_fwd > (size_t)smem_optin || P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
     int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H, P->zf);
     int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);

@@ -66,6 +66,10 @@ struct RowLaunch {
   int Mmax;
   int H;                       // half tap count (taps = 2H)
   int fft_region;              // complex values of shared memory used by the row slots (adjoint: nodes follow)
+  // adjoint only: sorted-bin spread buffers
+  int chunk;                   // nodes per bin chunk
+  int bin_offset;              // bytes from the start of dynamic shared memory to the bins
+  int bin_slot;                // bytes of bins per row slot: chunk * (2H+1) complex, 16-aligned
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)

@@ -594,22 +594,6 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
 // Adjoint
 // ---------------------------------------------------------------------------
 
-// One tap weight w_it(fr) from the shared-memory copy of the coefficients.
-template <int H>
-__device__ __forceinline__ float tap_weight(const float* sce, const float* sco, int it, float fr) {
-  const bool lo = it < H;
-  const int p = lo ? it : 2 * H - 1 - it;
-  const float z = lo ? (fr - 0.5f) : (0.5f - fr);
-  const float z2 = z * z;
-  float E = sce[(kHalfCoef - 1) * kMaxH + p], O = sco[(kHalfCoef - 1) * kMaxH + p];
-#pragma unroll
-  for (int e = kHalfCoef - 2; e >= 0; --e) {
-    E = fmaf(E, z2, sce[e * kMaxH + p]);
-    O = fmaf(O, z2, sco[e * kMaxH + p]);
-  }
-  return fmaf(z, O, E);
-}
-
 __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
@@ -621,12 +605,6 @@ template <int H, bool ZF>
 __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
-  __shared__ float sce[kHalfCoef * kMaxH], sco[kHalfCoef * kMaxH];
-  for (int i = threadIdx.x; i < kHalfCoef * kMaxH; i += blockDim.x) {
-    const int e = i / kMaxH, p = i - e * kMaxH;
-    sce[i] = W.ce[p][e];
-    sco[i] = W.co[p][e];
-  }
   float4* nodes_all = reinterpret_cast<float4*>(smem + L.fft_region);
   for (;;) {
     const int item = next_item(L.counter, &s_item);
@@ -724,44 +702,66 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
       }
     }
     __syncthreads();
-    if (valid) {
-      // phase 2: grid point j sums w_{j - j0}(fr) Q over nodes with j0 in [j - H, j + H - 1],
-      // including the periodic images j + m M.  Each thread owns 16 consecutive points.
-      const int a = lane * kElemsPerThread;
-      const int j0min = __float_as_int(N[0].x), j0max = __float_as_int(N[nn - 1].x);
-      float2 acc[kElemsPerThread];
-#pragma unroll
-      for (int q = 0; q < kElemsPerThread; ++q) acc[q] = make_float2(0.f, 0.f);
-      const int mlo = -floor_div(-(j0min - H - (kElemsPerThread - 2) - a), M);
-      const int mhi = floor_div(j0max + H - a, M);
-      for (int m = mlo; m <= mhi; ++m) {
-        const int g0 = a + m * M;
-        // first node with j0 >= g0 - H
-        int lo = 0, hi = nn;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (__float_as_int(N[mid].x) < g0 - H) lo = mid + 1;
-          else hi = mid;
-        }
-        int klo = lo, khi = lo;
-#pragma unroll
-        for (int q = 0; q < kElemsPerThread; ++q) {
-          const int g = g0 + q;
-          while (klo < nn && __float_as_int(N[klo].x) < g - H) ++klo;
-          if (khi < klo) khi = klo;
-          while (khi < nn && __float_as_int(N[khi].x) <= g + H - 1) ++khi;
-          float2 s = acc[q];
-          for (int k = klo; k < khi; ++k) {
-            const float4 nd = N[k];
-            const float w = tap_weight<H>(sce, sco, g - __float_as_int(nd.x) + H - 1, nd.y);
-            s.x = fmaf(w, nd.z, s.x);
-            s.y = fmaf(w, nd.w, s.y);
+    // phase 2: sorted-bin spread (the transpose of the gather).  Node k adds
+    // w_t(fr_k) Q_k to grid cell j0_k + t - H + 1 (mod M), t = 0..2H-1.
+    // Nodes are taken in chunks of at most one node per thread that never mix
+    // the two signs (-nu and +nu lists).  Nodes with equal j0 form a run (the
+    // list is sorted); for each tap t in turn the head of every run evaluates
+    // the tap weight of each of its nodes (tap index uniform over the CTA, so
+    // the polynomial coefficients stay constant-bank operands) and adds the
+    // run's sum to its cell.  Within a chunk distinct runs have distinct j0 and
+    // the chunk spans fewer than M - 2H cells, so in one tap phase no two heads
+    // write the same cell; a barrier separates the tap phases.  Every cell
+    // receives its terms in a fixed order (chunk, tap, node): deterministic, no
+    // atomics.
+    {
+      const int CH = L.chunk;  // <= tpr
+      for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
+      const int half_chunks = ((P.nz >> 1) + CH - 1) / CH;  // uniform over the CTA's slots
+      for (int c = 0; c < 2 * half_chunks; ++c) {
+        const bool pos = c >= half_chunks;
+        const int first = pos ? nneg : 0;
+        const int count = pos ? nn - nneg : nneg;
+        const int c0 = first + (pos ? c - half_chunks : c) * CH;
+        const int cn = valid ? max(0, min(CH, first + count - c0)) : 0;
+        int j0 = 0, run = 0;  // run length if this thread's node heads a run, else 0
+        if (lane < cn) {
+          j0 = __float_as_int(N[c0 + lane].x);
+          if (lane == 0 || __float_as_int(N[c0 + lane - 1].x) != j0) {
+            run = 1;
+            while (lane + run < cn && __float_as_int(N[c0 + lane + run].x) == j0) ++run;
           }
-          acc[q] = s;
+        }
+        __syncthreads();  // previous chunk's writes (or the zeroing) complete
+#pragma unroll
+        for (int t = 0; t < 2 * H; ++t) {
+          if (run > 0) {
+            // tap t of pair p: w(z) = E_p(z^2) +- z O_p(z^2), z = fr - 1/2 (sign + for t < H)
+            const int p = t < H ? t : 2 * H - 1 - t;
+            float sx = 0.f, sy = 0.f;
+            for (int r = 0; r < run; ++r) {
+              const float4 nd = N[c0 + lane + r];
+              const float z = t < H ? nd.y - 0.5f : 0.5f - nd.y;
+              const float z2 = z * z;
+              float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+              for (int e = kHalfCoef - 2; e >= 0; --e) {
+                E = fmaf(E, z2, W.ce[p][e]);
+                O = fmaf(O, z2, W.co[p][e]);
+              }
+              const float w = fmaf(z, O, E);
+              sx = fmaf(w, nd.z, sx);
+              sy = fmaf(w, nd.w, sy);
+            }
+            const int gi = PADI((j0 + t - H + 1) & mask);
+            float2 x = X[gi];
+            x.x += sx;
+            x.y += sy;
+            X[gi] = x;
+          }
+          __syncthreads();
         }
       }
-#pragma unroll
-      for (int q = 0; q < kElemsPerThread; ++q) X[PADI(a + q)] = acc[q];
     }
     __syncthreads();
     fft_smem<true, kLayoutFlat>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
