@@ -94,9 +94,10 @@ typedef struct {
   long long nodes;        /* nodes evaluated per call (sum over the batch)      */
   size_t workspace_bytes; /* device bytes owned by the plan                     */
   int uses_graph;         /* 1 if calls replay a captured CUDA graph            */
-  int library_ffts;       /* 1 if every stage runs on the library's own kernels
-                             (power-of-two sizes, chosen by the tuner), 0 if the
-                             inverse / adjoint image transforms use cuFFT       */
+  int library_ffts;       /* bit 0: pai_reconstruct runs every stage on the
+                             library's own kernels (power-of-two sizes, chosen
+                             by the tuner), else its inverse uses cuFFT; bit 1:
+                             the same for pai_adjoint                          */
 } pai_plan_info;
 
 /* Create a plan for one reconstruction problem (Algorithm 2).

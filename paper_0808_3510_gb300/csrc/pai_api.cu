@@ -62,7 +62,8 @@ struct pai_plan_s {
   int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
   int chunk = 128, bin_offset = 0, bin_slot = 0;  // adjoint sorted-bin spread
-  bool zf = false;  // every stage by the library's kernels: lateral FFTs + depth-fused row kernels
+  bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
+  bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
   WindowPoly poly{};
   double beta = 0, pred_err = 0, fit_err = 0;
@@ -90,6 +91,7 @@ struct pai_plan_s {
   std::vector<GraphEntry> graphs;
   long long own_kernels = 0, fft_execs = 0;
   int own_kernels_per_call = 0, fft_per_call = 0;
+  int own_kernels_per_adj = 0, fft_per_adj = 0;
 };
 
 namespace {
@@ -279,7 +281,7 @@ pai_status enqueue_inverse(pai_plan_s* P, const ProblemHost& p, float* d_f, cuda
 
 // First and last stages of the adjoint for problem p.
 pai_status enqueue_adj_first(pai_plan_s* P, const ProblemHost& p, const float* d_h, cudaStream_t s) {
-  if (P->zf) {
+  if (P->zf_adj) {
     PAI_TRY(own_lateral_fwd(P, p, d_h + p.img_off, P->d_fh + p.fh_off, p.g.nz, s));
     return cuda_status(launch_rows_c2c(P->d_fh + p.fh_off, p.g.nz, p.rows, false, P->d_tw, P->TW / p.g.nz, s));
   }
@@ -287,7 +289,7 @@ pai_status enqueue_adj_first(pai_plan_s* P, const ProblemHost& p, const float* d
 }
 
 pai_status enqueue_adj_last(pai_plan_s* P, const ProblemHost& p, float* d_pbar, cudaStream_t s) {
-  if (P->zf) return own_lateral_inv(P, p, P->d_pt + p.pt_off, d_pbar + p.data_off, p.g.nt, s);
+  if (P->zf_adj) return own_lateral_inv(P, p, P->d_pt + p.pt_off, d_pbar + p.data_off, p.g.nt, s);
   return fft_status(cufftExecC2R(p.lat_c2r, (cufftComplex*)(P->d_pt + p.pt_off), d_pbar + p.data_off));
 }
 
@@ -305,7 +307,7 @@ pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStre
 
 pai_status enqueue_adjoint(pai_plan_s* P, const float* d_h, float* d_pbar, cudaStream_t s) {
   for (auto& p : P->probs) PAI_TRY(enqueue_adj_first(P, p, d_h, s));
-  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj, P->zf));
+  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj, P->zf_adj));
   for (auto& p : P->probs) PAI_TRY(enqueue_adj_last(P, p, d_pbar, s));
   return PAI_OK;
 }
@@ -354,8 +356,8 @@ pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
     if (st == PAI_OK) st = cuda_status(cudaGraphLaunch(hit->exec, P->stream));
   }
   if (st == PAI_OK) {
-    P->own_kernels += P->own_kernels_per_call;
-    P->fft_execs += P->fft_per_call;
+    P->own_kernels += adjoint ? P->own_kernels_per_adj : P->own_kernels_per_call;
+    P->fft_execs += adjoint ? P->fft_per_adj : P->fft_per_call;
   }
   if (prev != P->device) cudaSetDevice(prev);
   return st;
@@ -435,6 +437,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       zf = zf && nz_ok && lat_ok;
     }
     P->zf = zf;
+    P->zf_adj = zf;
   }
 
   // ---- layout -------------------------------------------------------------
@@ -636,25 +639,32 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     float ms_zf = 1e30f, ms_cufft = 1e30f;
     if (cudaMalloc(&d_in, P->data_total * sizeof(float)) == cudaSuccess &&
         cudaMalloc(&d_out, P->img_total * sizeof(float)) == cudaSuccess &&
-        cudaMemset(d_in, 0, P->data_total * sizeof(float)) == cudaSuccess) {
+        cudaMemset(d_in, 0, P->data_total * sizeof(float)) == cudaSuccess &&
+        cudaMemset(d_out, 0, P->img_total * sizeof(float)) == cudaSuccess) {
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
-      for (int variant = 0; variant < 2; ++variant) {
-        P->zf = variant == 0;
+      float adj_zf = 1e30f, adj_cufft = 1e30f;
+      for (int variant = 0; variant < 4; ++variant) {
+        const bool adjoint = variant >= 2;
+        P->zf = P->zf_adj = (variant % 2) == 0;
         float best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, P->cap_stream);
           set_fft_streams(P, P->cap_stream);
-          if (enqueue_forward(P, d_in, d_out, P->cap_stream, false) != PAI_OK) break;
+          pai_status st = adjoint ? enqueue_adjoint(P, d_out, d_in, P->cap_stream)
+                                  : enqueue_forward(P, d_in, d_out, P->cap_stream, false);
+          if (st != PAI_OK) break;
           cudaEventRecord(e1, P->cap_stream);
           cudaEventSynchronize(e1);
           float ms = 0;
           cudaEventElapsedTime(&ms, e0, e1);
           if (rep > 0) best = std::min(best, ms);
         }
-        (variant == 0 ? ms_zf : ms_cufft) = best;
+        if (adjoint) (variant == 2 ? adj_zf : adj_cufft) = best;
+        else (variant == 0 ? ms_zf : ms_cufft) = best;
       }
+      P->zf_adj = adj_zf <= adj_cufft;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       set_fft_streams(P, P->stream);
@@ -663,6 +673,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     cudaFree(d_out);
     cudaGetLastError();
     P->zf = ms_zf <= ms_cufft;
+    if (ms_zf >= 1e29f && ms_cufft >= 1e29f) P->zf = P->zf_adj = true;
     if (!P->zf) {
       int own_lat = 0;
       for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
@@ -681,6 +692,15 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     for (auto& p : P->probs) own_lat += p.own_lateral ? 1 : 0;
     P->own_kernels_per_call = 1 + own_lat;  // the row kernel and the library's lateral kernels
     P->fft_per_call = 2 * count - own_lat;
+  }
+  if (P->zf_adj) {
+    int k = 1;
+    for (auto& p : P->probs) k += (p.g.dim == 2) ? 3 : 5;
+    P->own_kernels_per_adj = k;
+    P->fft_per_adj = 0;
+  } else {
+    P->own_kernels_per_adj = 1;
+    P->fft_per_adj = 2 * count;
   }
   PAI_CUDA(cudaDeviceSynchronize());
   guard.p = nullptr;
@@ -779,7 +799,7 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
     if (st == PAI_OK)
       st = enqueue_row(plan, adjoint != 0, s, plan->threads, adjoint ? plan->ctas_adj : plan->ctas,
-                       adjoint ? plan->smem_adj : plan->smem_fwd, plan->zf);
+                       adjoint ? plan->smem_adj : plan->smem_fwd, adjoint ? plan->zf_adj : plan->zf);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[2], s));
     for (auto& p : plan->probs) {
       if (st != PAI_OK) break;
@@ -793,8 +813,8 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
       acc[k] += t;
     }
     if (st == PAI_OK) {
-      plan->own_kernels += plan->own_kernels_per_call;
-      plan->fft_execs += plan->fft_per_call;
+      plan->own_kernels += adjoint ? plan->own_kernels_per_adj : plan->own_kernels_per_call;
+      plan->fft_execs += adjoint ? plan->fft_per_adj : plan->fft_per_call;
     }
   }
   for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
@@ -826,7 +846,7 @@ pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info) {
   info->nodes = plan->nodes;
   info->workspace_bytes = plan->ws_bytes;
   info->uses_graph = plan->use_graph ? 1 : 0;
-  info->library_ffts = plan->zf ? 1 : 0;
+  info->library_ffts = (plan->zf ? 1 : 0) | (plan->zf_adj ? 2 : 0);
   return PAI_OK;
 }
 
