@@ -237,6 +237,28 @@ def recorded_traffic(config: str):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (replicas: one independent problem per rank)
+# ---------------------------------------------------------------------------
+
+def aggregate_over_ranks(ms_local: float, voxels_local: int, device=None):
+    """Whole-job numbers for independent replicas: the step time is the max over
+    ranks, the throughput is the voxels all ranks reconstructed per step divided
+    by that time.  Works with any torch.distributed backend (gloo / nccl); with
+    no process group it is the single-rank case."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, voxels_local / (ms_local * 1e-3)
+    t = torch.tensor([ms_local, float(voxels_local)], dtype=torch.float64, device=device)
+    m = t[:1].clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    s = t[1:].clone()
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    ms_max = float(m.item())
+    return ms_max, float(s.item()) / (ms_max * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
 
@@ -379,12 +401,7 @@ def main():
     time.sleep(0.2)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = vox * world / (ms_max * 1e-3)
+    ms_max, value = aggregate_over_ranks(ms, vox, dev)
 
     # roofline of the row kernel
     st = plan.profile_stages(p, out, reps=50)
