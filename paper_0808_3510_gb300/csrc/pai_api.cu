@@ -82,6 +82,13 @@ struct pai_plan_s {
   int nitems_adj = 0;
   int* d_counter = nullptr;
   void* d_cufft_work = nullptr;
+  // batched plans: per-problem stages fork over branch streams (problem i on
+  // branch i % nbranch), each branch with its own cuFFT work area
+  int nbranch = 1;
+  std::vector<cudaStream_t> branch;
+  std::vector<void*> branch_work;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   size_t cufft_work = 0;
   size_t ws_bytes = 0;
   // host staging for pai_reconstruct_host
@@ -201,6 +208,10 @@ void release(pai_plan_s* P) {
   cudaFree(P->d_items_adj);
   cudaFree(P->d_counter);
   cudaFree(P->d_cufft_work);
+  for (void* w : P->branch_work) cudaFree(w);
+  for (cudaStream_t s : P->branch) cudaStreamDestroy(s);
+  for (cudaEvent_t e : P->ev_join) cudaEventDestroy(e);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   cudaFree(P->d_stage_in);
   cudaFree(P->d_stage_out);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
@@ -209,6 +220,7 @@ void release(pai_plan_s* P) {
 }
 
 pai_status set_fft_streams(pai_plan_s* P, cudaStream_t s) {
+  if (P->nbranch > 1) return PAI_OK;  // batched plans keep their plans on the branch streams
   for (auto& p : P->probs) {
     PAI_FFT(cufftSetStream(p.lat_r2c, s));
     PAI_FFT(cufftSetStream(p.lat_c2r, s));
@@ -293,23 +305,64 @@ pai_status enqueue_adj_last(pai_plan_s* P, const ProblemHost& p, float* d_pbar, 
   return fft_status(cufftExecC2R(p.lat_c2r, (cufftComplex*)(P->d_pt + p.pt_off), d_pbar + p.data_off));
 }
 
+// Per-problem stages of a batched plan run on the branch streams: fork from s,
+// enqueue problem i on branch i % nbranch, join back into s.
+pai_status fork(pai_plan_s* P, cudaStream_t s) {
+  if (P->nbranch <= 1) return PAI_OK;
+  PAI_CUDA(cudaEventRecord(P->ev_fork, s));
+  for (auto b : P->branch) PAI_CUDA(cudaStreamWaitEvent(b, P->ev_fork, 0));
+  return PAI_OK;
+}
+
+pai_status join(pai_plan_s* P, cudaStream_t s) {
+  if (P->nbranch <= 1) return PAI_OK;
+  for (int b = 0; b < P->nbranch; ++b) {
+    PAI_CUDA(cudaEventRecord(P->ev_join[b], P->branch[b]));
+    PAI_CUDA(cudaStreamWaitEvent(s, P->ev_join[b], 0));
+  }
+  return PAI_OK;
+}
+
+cudaStream_t stream_of(pai_plan_s* P, size_t i, cudaStream_t s) {
+  return P->nbranch > 1 ? P->branch[i % P->nbranch] : s;
+}
+
+// The per-problem first stage (forward: lateral R2C of the data; adjoint:
+// image-side transforms) and last stage (forward: inverse; adjoint: lateral
+// C2R), forked over the branch streams of a batched plan.
+pai_status enqueue_first(pai_plan_s* P, const float* in, cudaStream_t s, bool adjoint) {
+  PAI_TRY(fork(P, s));
+  for (size_t i = 0; i < P->probs.size(); ++i) {
+    const cudaStream_t si = stream_of(P, i, s);
+    PAI_TRY(adjoint ? enqueue_adj_first(P, P->probs[i], in, si) : enqueue_lateral(P, P->probs[i], in, si));
+  }
+  return join(P, s);
+}
+
+pai_status enqueue_last(pai_plan_s* P, float* out, cudaStream_t s, bool adjoint) {
+  PAI_TRY(fork(P, s));
+  for (size_t i = 0; i < P->probs.size(); ++i) {
+    const cudaStream_t si = stream_of(P, i, s);
+    PAI_TRY(adjoint ? enqueue_adj_last(P, P->probs[i], out, si) : enqueue_inverse(P, P->probs[i], out, si));
+  }
+  return join(P, s);
+}
+
 // Stages (a)-(c) for the forward operator, enqueued on s.  spectrum_only
 // stops after the row stage with the half image spectrum in d_fh (always the
 // non-fused row kernel).
 pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStream_t s, bool spectrum_only) {
-  for (auto& p : P->probs) PAI_TRY(enqueue_lateral(P, p, d_p, s));
+  PAI_TRY(enqueue_first(P, d_p, s, false));
   const bool zf = P->zf && !spectrum_only;
   PAI_TRY(enqueue_row(P, false, s, P->threads, P->ctas, P->smem_fwd, zf));
-  if (!spectrum_only)
-    for (auto& p : P->probs) PAI_TRY(enqueue_inverse(P, p, d_f, s));
+  if (!spectrum_only) PAI_TRY(enqueue_last(P, d_f, s, false));
   return PAI_OK;
 }
 
 pai_status enqueue_adjoint(pai_plan_s* P, const float* d_h, float* d_pbar, cudaStream_t s) {
-  for (auto& p : P->probs) PAI_TRY(enqueue_adj_first(P, p, d_h, s));
+  PAI_TRY(enqueue_first(P, d_h, s, true));
   PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj, P->zf_adj));
-  for (auto& p : P->probs) PAI_TRY(enqueue_adj_last(P, p, d_pbar, s));
-  return PAI_OK;
+  return enqueue_last(P, d_pbar, s, true);
 }
 
 pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
@@ -516,16 +569,38 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   size_t work = 0;
   for (auto& p : P->probs) PAI_TRY(make_cufft_plans(p, work));
   P->cufft_work = work;
-  if (work) {
-    PAI_CUDA(cudaMalloc(&P->d_cufft_work, work));
-    for (auto& p : P->probs) {
-      PAI_FFT(cufftSetWorkArea(p.lat_r2c, P->d_cufft_work));
-      PAI_FFT(cufftSetWorkArea(p.lat_c2r, P->d_cufft_work));
-      PAI_FFT(cufftSetWorkArea(p.img_c2r, P->d_cufft_work));
-      PAI_FFT(cufftSetWorkArea(p.img_r2c, P->d_cufft_work));
+  P->nbranch = std::min(count, 8);
+  if (P->nbranch > 1) {
+    P->branch.resize(P->nbranch, nullptr);
+    P->branch_work.resize(P->nbranch, nullptr);
+    P->ev_join.resize(P->nbranch, nullptr);
+    PAI_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    for (int b = 0; b < P->nbranch; ++b) {
+      PAI_CUDA(cudaStreamCreateWithFlags(&P->branch[b], cudaStreamNonBlocking));
+      PAI_CUDA(cudaEventCreateWithFlags(&P->ev_join[b], cudaEventDisableTiming));
+      if (work) PAI_CUDA(cudaMalloc(&P->branch_work[b], work));
     }
+    for (size_t i = 0; i < P->probs.size(); ++i) {
+      auto& p = P->probs[i];
+      const int b = (int)(i % P->nbranch);
+      for (cufftHandle h : {p.lat_r2c, p.lat_c2r, p.img_c2r, p.img_r2c}) {
+        if (work) PAI_FFT(cufftSetWorkArea(h, P->branch_work[b]));
+        PAI_FFT(cufftSetStream(h, P->branch[b]));
+      }
+    }
+    P->ws_bytes += work * P->nbranch;
+  } else {
+    if (work) {
+      PAI_CUDA(cudaMalloc(&P->d_cufft_work, work));
+      for (auto& p : P->probs) {
+        PAI_FFT(cufftSetWorkArea(p.lat_r2c, P->d_cufft_work));
+        PAI_FFT(cufftSetWorkArea(p.lat_c2r, P->d_cufft_work));
+        PAI_FFT(cufftSetWorkArea(p.img_c2r, P->d_cufft_work));
+        PAI_FFT(cufftSetWorkArea(p.img_r2c, P->d_cufft_work));
+      }
+    }
+    P->ws_bytes += work;
   }
-  P->ws_bytes += work;
   PAI_TRY(set_fft_streams(P, P->stream));
 
   // ---- work items and launch shape ------------------------------------------
@@ -792,19 +867,13 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
   cudaStream_t s = plan->stream;
   for (int r = 0; r < reps && st == PAI_OK; ++r) {
     st = cuda_status(cudaEventRecord(ev[0], s));
-    for (auto& p : plan->probs) {
-      if (st != PAI_OK) break;
-      st = adjoint ? enqueue_adj_first(plan, p, d_in, s) : enqueue_lateral(plan, p, d_in, s);
-    }
+    if (st == PAI_OK) st = enqueue_first(plan, d_in, s, adjoint != 0);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
     if (st == PAI_OK)
       st = enqueue_row(plan, adjoint != 0, s, plan->threads, adjoint ? plan->ctas_adj : plan->ctas,
                        adjoint ? plan->smem_adj : plan->smem_fwd, adjoint ? plan->zf_adj : plan->zf);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[2], s));
-    for (auto& p : plan->probs) {
-      if (st != PAI_OK) break;
-      st = adjoint ? enqueue_adj_last(plan, p, d_out, s) : enqueue_inverse(plan, p, d_out, s);
-    }
+    if (st == PAI_OK) st = enqueue_last(plan, d_out, s, adjoint != 0);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[3], s));
     if (st == PAI_OK) st = cuda_status(cudaEventSynchronize(ev[3]));
     for (int k = 0; k < 3 && st == PAI_OK; ++k) {
