@@ -77,7 +77,25 @@ typedef struct {
   double alpha;         /* Kaiser-Bessel shape; 0 -> pi*(2c_os - 1)*(1 - 1e-3),
                            must be < pi*(2c_os - 1) (Lemma on Fourmont's
                            identity).                                        */
+  int method;           /* how the temporal spectrum is evaluated at the nodes
+                           (paper Sec. 4, the compared Fourier algorithms):
+                           PAI_METHOD_KB (0, default): Algorithm 1 with the
+                             Kaiser-Bessel window;
+                           PAI_METHOD_TSINC: Algorithm 1 with the indicator
+                             window of [-c pi, c pi] (truncated sinc, taps
+                             2 ceil(c K), K default 3);
+                           PAI_METHOD_LINEAR / PAI_METHOD_NEAREST: the exact
+                             oversampled DFT at omega = j/c (no window),
+                             interpolated linearly / to the nearest node;
+                             oversampling may be 1 (no oversampling).
+                           pai_adjoint supports KB and TSINC only.  All problems
+                           of a batch use the same method.                   */
 } pai_geometry;
+
+#define PAI_METHOD_KB 0
+#define PAI_METHOD_TSINC 1
+#define PAI_METHOD_LINEAR 2
+#define PAI_METHOD_NEAREST 3
 
 /* Read-only description of a plan (for reports and tests). */
 typedef struct {
@@ -85,9 +103,12 @@ typedef struct {
   int M;                  /* padded temporal FFT length of problem 0            */
   int taps;               /* taps per node (2*ceil(c_os*K))                      */
   double oversampling;    /* effective c_os = M/nt of problem 0                  */
-  double K, alpha;        /* effective window parameters of problem 0           */
+  double K, alpha;        /* effective window parameters of problem 0 (alpha is
+                             0 and K the tap half-width for the truncated sinc;
+                             both 0 for the interpolation methods)             */
   double predicted_error; /* FP64 truncation error of the window identity (max
-                             over the batch), see pai_plan                       */
+                             over the batch), see pai_plan; -1 for the
+                             interpolation methods, which have no such bound     */
   int threads_per_cta;    /* row-kernel CTA size chosen by the tuner             */
   int ctas;               /* row-kernel grid size (persistent CTAs)              */
   int rows;               /* lateral-frequency rows processed per call          */
@@ -107,14 +128,17 @@ typedef struct {
  * out:         receives the plan on success.
  * Synchronises the device.  Validation (PAI_ERR_INVALID_ARG): dim in {2,3};
  * nx, nz, nt even and >= 2 (ny even and >= 2 in 3-D); spacings, dt and c > 0;
- * oversampling == 0 or > 1; K >= 0; 0 <= alpha < pi*(2 c_os_eff - 1).        */
+ * oversampling == 0 or > 1 (== 1 also allowed for PAI_METHOD_LINEAR and
+ * PAI_METHOD_NEAREST); K >= 0; 0 <= alpha < pi*(2 c_os_eff - 1); method in
+ * PAI_METHOD_KB..PAI_METHOD_NEAREST.                                         */
 pai_status pai_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out);
 
 /* Create one plan for `count` independent 2-D or 3-D problems (g[0..count-1])
  * executed together: one lateral FFT per problem, ONE persistent row-kernel
  * launch over every lateral-frequency row of every problem, one inverse FFT
  * per problem, all replayed as one CUDA graph.  The problems share the tap
- * count (the largest over the batch); each keeps its own oversampling.
+ * count (the largest over the batch) and the method (PAI_ERR_INVALID_ARG
+ * otherwise); each keeps its own oversampling.
  * Data and images of the batch are concatenated in g-order.                  */
 pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream, pai_plan_t* out);
 
@@ -129,7 +153,10 @@ pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f);
  * forward image FFT, window spread from the nodes onto the oversampled grid
  * in gather form, inverse oversampled FFT, prescale, inverse lateral FFT).
  * d_h: device, FP32, image-shaped, read only.  d_pbar: device, FP32,
- * data-shaped, overwritten.  Asynchronous on the plan's stream.              */
+ * data-shaped, overwritten.  Asynchronous on the plan's stream.
+ * PAI_ERR_UNSUPPORTED for plans of the interpolation methods (linear,
+ * nearest): the transposed spread exists for the windowed methods (KB,
+ * truncated sinc) only.                                                      */
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar);
 
 /* The image spectrum before the inverse FFT: steps 1-3 of Algorithm 2.

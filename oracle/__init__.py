@@ -79,6 +79,8 @@ def _load():
         lib.oracle_node.restype = ctypes.c_double
         lib.oracle_weight.argtypes = [G, i, i, i]
         lib.oracle_weight.restype = ctypes.c_double
+        lib.oracle_row_nodes.argtypes = [G, i, i, dp, dp]
+        lib.oracle_row_nodes.restype = None
         lib.oracle_nudft.argtypes = [i, dp, i, dp, dp]
         lib.oracle_nudft.restype = None
         lib.oracle_nudft_adjoint.argtypes = [i, dp, i, dp, dp]
@@ -129,6 +131,16 @@ def weight(g, kx: int, ky: int, l: int) -> float:
     """Weight of Eq. (fft-0) in the general grid (0 on the l = 0 row)."""
     gg = _geom(g)
     return _load().oracle_weight(ctypes.byref(gg), kx, ky, l)
+
+
+def row_nodes(g, kx: int, ky: int = 0):
+    """Nodes and weights of one lateral row for every depth frequency, storage
+    index l mod nz: the values of :func:`node` and :func:`weight`."""
+    gg = _geom(g)
+    nu = np.empty(gg.nz, np.float64)
+    w = np.empty(gg.nz, np.float64)
+    _load().oracle_row_nodes(ctypes.byref(gg), kx, ky, _dptr(nu), _dptr(w))
+    return nu, w
 
 
 def nudft(gvec: np.ndarray, nu: np.ndarray) -> np.ndarray:

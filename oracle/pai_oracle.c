@@ -147,6 +147,15 @@ double oracle_weight(const oracle_geom* g, int kx, int ky, int l) {
   return g->c * (g->dt / g->dz) * 2.0 * Kz / k_norm(g, kx, ky, l);
 }
 
+/* all nodes and weights of one lateral row, storage index l mod nz */
+void oracle_row_nodes(const oracle_geom* g, int kx, int ky, double* nu, double* w) {
+  for (int li = 0; li < g->nz; ++li) {
+    int l = signed_freq(li, g->nz);
+    nu[li] = oracle_node(g, kx, ky, l);
+    w[li] = oracle_weight(g, kx, ky, l);
+  }
+}
+
 /* ------------------------------------------------------------------ */
 /* Eq. (dft): direct DFT of one vector at arbitrary nodes               */
 /* ------------------------------------------------------------------ */

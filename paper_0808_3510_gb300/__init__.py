@@ -53,7 +53,25 @@ class Geometry(ctypes.Structure):
         ("nt", ctypes.c_int), ("dt", ctypes.c_double), ("c", ctypes.c_double),
         ("nz", ctypes.c_int), ("dz", ctypes.c_double),
         ("oversampling", ctypes.c_double), ("K", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("method", ctypes.c_int),
     ]
+
+
+# How the temporal spectrum is evaluated at the nodes (the Fourier algorithms
+# compared in Sec. 4): Algorithm 1 with the Kaiser-Bessel window (default) or
+# with the indicator window (truncated sinc), or the exact oversampled DFT
+# interpolated linearly / to the nearest grid node.
+METHODS = {"kb": 0, "tsinc": 1, "linear": 2, "nearest": 3}
+
+
+def method_code(m) -> int:
+    if m is None:
+        return 0
+    if isinstance(m, str):
+        if m not in METHODS:
+            raise ValueError(f"unknown method {m!r}; expected one of {sorted(METHODS)}")
+        return METHODS[m]
+    return int(m)
 
 
 class PlanInfo(ctypes.Structure):
@@ -125,7 +143,8 @@ def _check(status: int, where: str):
 
 def geometry(g) -> Geometry:
     """Build a ``pai_geometry`` from a dict or an object with the same field names
-    (dim, nx, ny, dx, dy, nt, dt, c, nz, dz; optional oversampling, K, alpha)."""
+    (dim, nx, ny, dx, dy, nt, dt, c, nz, dz; optional oversampling, K, alpha and
+    method, a name from ``METHODS`` or its code)."""
     get = (lambda k, d=None: g.get(k, d)) if isinstance(g, dict) else (lambda k, d=None: getattr(g, k, d))
     dim = int(get("dim"))
     return Geometry(
@@ -134,6 +153,7 @@ def geometry(g) -> Geometry:
         int(get("nt")), float(get("dt", 1.0)), float(get("c", 1.0)),
         int(get("nz")), float(get("dz", 1.0)),
         float(get("oversampling", 0.0) or 0.0), float(get("K", 0.0) or 0.0), float(get("alpha", 0.0) or 0.0),
+        method_code(get("method", 0)),
     )
 
 

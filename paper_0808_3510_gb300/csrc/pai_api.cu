@@ -62,6 +62,7 @@ struct pai_plan_s {
   int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
   int chunk = 128, bin_offset = 0, bin_slot = 0;  // adjoint sorted-bin spread
+  int method = PAI_METHOD_KB;                       // PAI_METHOD_*, shared by the batch
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
   bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
@@ -420,6 +421,8 @@ pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
 pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_s** out) {
   if (!gs || !out || count < 1) return PAI_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) PAI_TRY(validate(gs[i]));
+  for (int i = 1; i < count; ++i)
+    if (gs[i].method != gs[0].method) return PAI_ERR_INVALID_ARG;  // one evaluation method per plan
   pai_plan_s* P = new (std::nothrow) pai_plan_s();
   if (!P) return PAI_ERR_OOM;
   struct Guard {
@@ -444,20 +447,49 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->Mmax = std::max(P->Mmax, p.M);
     c_min = std::min(c_min, p.c_eff);
   }
-  // one window shape for the whole plan: common H and beta
-  bool user_alpha = count == 1 && gs[0].alpha > 0;
-  P->beta = user_alpha ? P->probs[0].beta : kPi * (2.0 - 1.0 / c_min) * (1.0 - 1e-3);
-  for (auto& p : P->probs) {
-    p.H = P->H;
-    p.beta = P->beta;
-    p.K_eff = p.H / p.c_eff;
-    p.alpha_eff = p.beta * p.c_eff;
-    if (!(p.alpha_eff > kPi) || !(p.alpha_eff < kPi * (2 * p.c_eff - 1))) return PAI_ERR_INVALID_ARG;
-    p.pred_err = predicted_error(p.c_eff, p.H, p.beta);
-    P->pred_err = std::max(P->pred_err, p.pred_err);
+  P->method = gs[0].method;
+  if (P->method == PAI_METHOD_KB) {
+    // one window shape for the whole plan: common H and beta
+    bool user_alpha = count == 1 && gs[0].alpha > 0;
+    P->beta = user_alpha ? P->probs[0].beta : kPi * (2.0 - 1.0 / c_min) * (1.0 - 1e-3);
+    for (auto& p : P->probs) {
+      p.H = P->H;
+      p.beta = P->beta;
+      p.K_eff = p.H / p.c_eff;
+      p.alpha_eff = p.beta * p.c_eff;
+      if (!(p.alpha_eff > kPi) || !(p.alpha_eff < kPi * (2 * p.c_eff - 1))) return PAI_ERR_INVALID_ARG;
+      p.pred_err = predicted_error(0, p.c_eff, p.H, p.beta);
+      P->pred_err = std::max(P->pred_err, p.pred_err);
+    }
+    P->fit_err = fit_window(0, P->H, P->beta, &P->poly);
+    if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
+  } else if (P->method == PAI_METHOD_TSINC) {
+    // the indicator window: a fixed shape, only the common tap count
+    P->beta = 0.0;
+    for (auto& p : P->probs) {
+      p.H = P->H;
+      p.beta = 0.0;
+      p.K_eff = p.H / p.c_eff;
+      p.alpha_eff = 0.0;
+      p.pred_err = predicted_error(1, p.c_eff, p.H, 0.0);
+      P->pred_err = std::max(P->pred_err, p.pred_err);
+    }
+    P->fit_err = fit_window(1, P->H, 0.0, &P->poly);
+    if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
+  } else {
+    // interpolation of the plain oversampled DFT: no window, no a-priori bound
+    P->beta = 0.0;
+    std::memset(&P->poly, 0, sizeof(P->poly));
+    P->fit_err = 0.0;
+    P->pred_err = -1.0;
+    for (auto& p : P->probs) {
+      p.H = P->H;
+      p.beta = 0.0;
+      p.K_eff = 0.0;
+      p.alpha_eff = 0.0;
+      p.pred_err = -1.0;
+    }
   }
-  P->fit_err = fit_window(P->H, P->beta, &P->poly);
-  if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
 
   // ---- CTA shape ----------------------------------------------------------
   int sms = 0;
@@ -720,7 +752,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       float adj_zf = 1e30f, adj_cufft = 1e30f;
-      for (int variant = 0; variant < 4; ++variant) {
+      const int nvariants = method_interp(P->method) ? 2 : 4;  // interpolation methods have no adjoint
+      for (int variant = 0; variant < nvariants; ++variant) {
         const bool adjoint = variant >= 2;
         P->zf = P->zf_adj = (variant % 2) == 0;
         float best = 1e30f;
@@ -804,6 +837,7 @@ pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f) {
 
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar) {
   if (!plan || !d_h || !d_pbar) return PAI_ERR_INVALID_ARG;
+  if (method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
   return run(plan, d_h, d_pbar, true);
 }
 
@@ -856,6 +890,7 @@ pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
 
 pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, int reps, int adjoint, double* ms) {
   if (!plan || !d_in || !d_out || !ms || reps < 1) return PAI_ERR_INVALID_ARG;
+  if (adjoint && method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
@@ -938,10 +973,10 @@ pai_status pai_window_probe(int H, double beta, double c, int n, const double* y
   if (n > 0 && (!y || !phi_out)) return PAI_ERR_INVALID_ARG;
   const double peak = kb_phi(0.0, H, beta);
   for (int i = 0; i < n; ++i) phi_out[i] = kb_phi(y[i], H, beta) / peak;
-  if (pred_err) *pred_err = predicted_error(c, H, beta);
+  if (pred_err) *pred_err = predicted_error(0, c, H, beta);
   if (fit_err) {
     WindowPoly w;
-    *fit_err = fit_window(H, beta, &w);
+    *fit_err = fit_window(0, H, beta, &w);
   }
   return PAI_OK;
 }

@@ -50,6 +50,7 @@ struct RowProblem {
   float nt_over_M;         // for the node phase
   int mshift;              // log2(M)
   int nzshift;             // log2(nz) when nz is a power of two, else 0
+  int method;              // PAI_METHOD_*
 };
 
 struct WorkItem {
@@ -81,18 +82,22 @@ double bessel_i0(double x);
 // Normalised window transform in grid units: phi(y) = sinh(beta sqrt(H^2 - y^2)) / sqrt(H^2 - y^2)
 // (analytic continuation sin(...) / ... for |y| > H).
 double kb_phi(double y, double H, double beta);
+// Window kinds: 0 Kaiser-Bessel, 1 indicator of [-c pi, c pi] (truncated sinc).
+double window_phi(int kind, double y, double H, double beta);
+double window_s(int kind, double theta, double c, int H, double beta);
 // Fit the tap polynomials; returns the max abs fit error relative to phi(0).
-double fit_window(int H, double beta, WindowPoly* out);
+double fit_window(int kind, int H, double beta, WindowPoly* out);
 // Truncation error of Fourmont's identity for (c, H, beta), max over theta and offsets.
-double predicted_error(double c, int H, double beta);
-// Prescale for sample n: 1 / (pi I0(H sqrt(beta^2 - (theta_n/c)^2))) * phi(0), theta_n = 2 pi n/nt - pi.
-void prescale_table(int nt, double c, int H, double beta, double extra, float* out);
+double predicted_error(int kind, double c, int H, double beta);
+// Prescale for sample n: s(theta_n) * phi(0) * extra, theta_n = 2 pi n/nt - pi.
+void prescale_table(int kind, int nt, double c, int H, double beta, double extra, float* out);
 
 // Plan-time parameters and tables shared by all entry points, pai_plan_math.cpp.
 // Functions returning int return pai_status values.
 struct ProblemParams {
   int M = 0, mshift = 0, H = 0;
   double c_eff = 0, beta = 0;
+  int method = 0;  // PAI_METHOD_*
 };
 void split_ff(double v, float& hi, float& lo);
 int validate_geometry(const pai_geometry& g);
@@ -102,6 +107,9 @@ void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d
 // prescale [nt], rowS [2 * rows] (float-float), zt [4 * (nz/2 + 1)].
 void fill_row_tables(const pai_geometry& g, double c_eff, int H, double beta, float* prescale, float* rowS,
                      float* zt);
+// Window kind used by a method (0 KB, 1 sinc) and whether the method gathers with a window at all.
+inline int method_window(int method) { return method == PAI_METHOD_TSINC ? 1 : 0; }
+inline bool method_interp(int method) { return method == PAI_METHOD_LINEAR || method == PAI_METHOD_NEAREST; }
 // Scalar fields of RowProblem (everything except pointers and rpc).
 void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r);
 void twiddle_table(int Mmax, float2* tw);

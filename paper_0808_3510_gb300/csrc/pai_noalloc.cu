@@ -56,6 +56,7 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   }
   int st = validate_geometry(g);
   if (st != PAI_OK) return (pai_status)st;
+  if (g.method != PAI_METHOD_KB) return PAI_ERR_UNSUPPORTED;
   ProblemParams pp;
   st = choose_problem_params(g, pp);
   if (st != PAI_OK) return (pai_status)st;
@@ -88,7 +89,7 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   if (used > kScratchBytes) return PAI_ERR_UNSUPPORTED;
 
   WindowPoly poly;
-  if (!(fit_window(pp.H, pp.beta, &poly) < 1e-6)) return PAI_ERR_UNSUPPORTED;
+  if (!(fit_window(0, pp.H, pp.beta, &poly) < 1e-6)) return PAI_ERR_UNSUPPORTED;
 
   std::lock_guard<std::mutex> lock(g_mutex);
   int dev = 0;

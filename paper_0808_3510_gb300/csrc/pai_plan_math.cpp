@@ -37,7 +37,9 @@ int validate_geometry(const pai_geometry& g) {
   if (g.dim == 3 && !is_even_pos(g.ny)) return PAI_ERR_INVALID_ARG;
   if (!(g.dx > 0) || !(g.dt > 0) || !(g.c > 0) || !(g.dz > 0)) return PAI_ERR_INVALID_ARG;
   if (g.dim == 3 && !(g.dy > 0)) return PAI_ERR_INVALID_ARG;
-  if (!(g.oversampling == 0 || g.oversampling > 1.0)) return PAI_ERR_INVALID_ARG;
+  if (g.method < PAI_METHOD_KB || g.method > PAI_METHOD_NEAREST) return PAI_ERR_INVALID_ARG;
+  if (!(g.oversampling == 0 || g.oversampling > 1.0 || (g.oversampling == 1.0 && method_interp(g.method))))
+    return PAI_ERR_INVALID_ARG;
   if (!(g.K >= 0) || !(g.alpha >= 0)) return PAI_ERR_INVALID_ARG;
   if (!std::isfinite(g.dx + g.dt + g.c + g.dz + g.oversampling + g.K + g.alpha)) return PAI_ERR_INVALID_ARG;
   if (g.dim == 3 && !std::isfinite(g.dy)) return PAI_ERR_INVALID_ARG;
@@ -50,12 +52,27 @@ int validate_geometry(const pai_geometry& g) {
 // "alpha slightly smaller than pi (2c - 1)"); half tap count H = ceil(c_os K)
 // or, with K = 0, the smallest H whose truncation error is <= 1e-8.
 int choose_problem_params(const pai_geometry& g, ProblemParams& p) {
+  p.method = g.method;
   const double c_req = g.oversampling > 0 ? g.oversampling : 2.0;
   long long want = (long long)std::ceil(c_req * g.nt - 1e-9);
   p.M = std::max(32, next_pow2(want));
   if (p.M > 16 * 1024) return PAI_ERR_UNSUPPORTED;
   p.mshift = ilog2(p.M);
   p.c_eff = (double)p.M / g.nt;
+  if (method_interp(g.method)) {
+    // no window: H only sizes the ghost cells the interpolation reads
+    p.beta = 0.0;
+    p.H = 2;
+    return PAI_OK;
+  }
+  if (g.method == PAI_METHOD_TSINC) {
+    p.beta = 0.0;
+    const double K = g.K > 0 ? g.K : 3.0;
+    p.H = (int)std::ceil(c_req * K - 1e-9);
+    if (p.H < 2) p.H = 2;
+    if (p.H > kMaxH) return PAI_ERR_UNSUPPORTED;
+    return PAI_OK;
+  }
   if (g.alpha > 0) {
     p.beta = g.alpha / c_req;
     if (!(g.alpha < kPi * (2 * c_req - 1))) return PAI_ERR_INVALID_ARG;
@@ -69,7 +86,7 @@ int choose_problem_params(const pai_geometry& g, ProblemParams& p) {
   } else {
     p.H = 0;
     for (int h = 2; h <= kMaxH; ++h)
-      if (predicted_error(p.c_eff, h, p.beta) <= 1e-8) {
+      if (predicted_error(0, p.c_eff, h, p.beta) <= 1e-8) {
         p.H = h;
         break;
       }
@@ -88,7 +105,11 @@ void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d
 
 void fill_row_tables(const pai_geometry& g, double c_eff, int H, double beta, float* prescale, float* rowS,
                      float* zt) {
-  prescale_table(g.nt, c_eff, H, beta, 1.0, prescale);
+  if (method_interp(g.method)) {
+    for (int n = 0; n < g.nt; ++n) prescale[n] = 1.0f;  // the plain oversampled DFT
+  } else {
+    prescale_table(method_window(g.method), g.nt, c_eff, H, beta, 1.0, prescale);
+  }
   int n1, n2;
   double d1, d2;
   lateral_axes(g, n1, n2, d1, d2);
@@ -131,6 +152,7 @@ void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r) {
   split_ff(B * B, r.B2hi, r.B2lo);
   r.wscale = (float)(2.0 * g.c * g.dt / g.dz * B / ((double)n1 * n2 * g.nz));
   r.nt_over_M = (float)((double)g.nt / M);
+  r.method = g.method;
 }
 
 void twiddle_table(int Mmax, float2* tw) {

@@ -418,6 +418,35 @@ __device__ __forceinline__ float2 node_value(const float2* U, const WindowPoly& 
   return make_float2(fmaf(ax, ph.x, ay * ph.y), fmaf(ay, ph.x, -ax * ph.y));
 }
 
+// Interpolation methods of Sec. 4 (no window, prescale 1): the oversampled DFT
+// D_j = sum_n e^{-2 pi i j n / M} g_n sits on the grid nu_j = j nt / M, and the
+// centred spectrum holds U[j] = e^{+i pi nu_j} D_j, so D_j = e^{-i pi nu_j} U[j mod M].
+// LINEAR: (1 - fr) D_j0 + fr D_{j0+1};  NEAREST: D_{j0 + (fr >= 1/2)}.
+__device__ __forceinline__ float2 grid_value(const float2* U, int j, int M, int nt, float nt_over_M) {
+  const float2 u = U[j & (M - 1)];
+  const float2 ph = node_phase(j, 0.0f, nt, M, nt_over_M);
+  return make_float2(fmaf(u.x, ph.x, u.y * ph.y), fmaf(u.y, ph.x, -u.x * ph.y));
+}
+
+__device__ __forceinline__ float2 node_interp(const float2* U, int method, int j0, float fr, int M, int nt,
+                                              float nt_over_M) {
+  if (method == PAI_METHOD_NEAREST) return grid_value(U, j0 + (fr >= 0.5f ? 1 : 0), M, nt, nt_over_M);
+  const float2 a = grid_value(U, j0, M, nt, nt_over_M);
+  const float2 b = grid_value(U, j0 + 1, M, nt, nt_over_M);
+  return make_float2(fmaf(fr, b.x - a.x, a.x), fmaf(fr, b.y - a.y, a.y));
+}
+
+// The value at a node by the problem's method.  Interpolation plans always run
+// with H = 2, so the other instantiations carry no method branch.
+template <int H>
+__device__ __forceinline__ float2 node_eval(const RowProblem& P, const float2* U, const WindowPoly& W, int j0,
+                                            float fr) {
+  if constexpr (H == 2) {
+    if (P.method >= PAI_METHOD_LINEAR) return node_interp(U, P.method, j0, fr, P.M, P.nt, P.nt_over_M);
+  }
+  return node_value<H>(U, W, j0, fr, P.M, P.nt, P.nt_over_M);
+}
+
 struct RowGeom {
   int d1, d2;     // destination rows (full lateral index) of +nu and -nu nodes
   bool mirror;    // row is not self-conjugate: both destinations are written
@@ -486,10 +515,10 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
     node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
     const float wt = P.wscale * zt.z / x0;
     if (!neg) {
-      float2 v = node_value<H>(X, W, j0p, frp, P.M, P.nt, P.nt_over_M);
+      float2 v = node_eval<H>(P, X, W, j0p, frp);
       if (nyq) {
         negate_node(j0p, frp, j0, fr);
-        float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+        float2 u = node_eval<H>(P, X, W, j0, fr);
         float2 a = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
         out1[lp] = a;
         if (rg.mirror) out2[lp] = make_float2(a.x, -a.y);
@@ -498,7 +527,7 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
       }
     } else {
       negate_node(j0p, frp, j0, fr);
-      float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+      float2 u = node_eval<H>(P, X, W, j0, fr);
       out2[lp] = make_float2(wt * u.x, -wt * u.y);
     }
   }
@@ -538,17 +567,17 @@ __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPo
     node_position(S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
     const float wt = P.wscale * zt.z / x0;
     if (!neg) {
-      const float2 v = node_value<H>(X, W, j0p, frp, P.M, P.nt, P.nt_over_M);
+      const float2 v = node_eval<H>(P, X, W, j0p, frp);
       if (nyq) {
         negate_node(j0p, frp, j0, fr);
-        const float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+        const float2 u = node_eval<H>(P, X, W, j0, fr);
         Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
       } else {
         Zs[lp] = make_float2(wt * v.x, wt * v.y);
       }
     } else {
       negate_node(j0p, frp, j0, fr);
-      const float2 u = node_value<H>(X, W, j0, fr, P.M, P.nt, P.nt_over_M);
+      const float2 u = node_eval<H>(P, X, W, j0, fr);
       Zs[P.nz - lp] = make_float2(wt * u.x, wt * u.y);
     }
   }

@@ -52,6 +52,28 @@ double kb_phi(double y, double H, double beta) {
   return std::sin(a) / s;
 }
 
+// The window transform of the requested kind in grid units, and the factor
+// s(theta) of the identity e^{-i omega theta} = s(theta) sum_j phi(c omega - j) e^{-i j theta / c}:
+//   Kaiser-Bessel: phi as above, s = 1 / (pi I0(H sqrt(beta^2 - (theta/c)^2)));
+//   indicator of [-c pi, c pi] (truncated sinc): psi_hat(u) = 2 sin(c pi u) / u,
+//     so with 1/(2 pi c) and psi = 1 on [-pi, pi]: phi(y) = sin(pi y) / (pi y), s = 1.
+double window_phi(int kind, double y, double H, double beta) {
+  if (kind == 1) {
+    const double pi = 3.14159265358979323846;
+    if (std::fabs(y) < 1e-8) return 1.0 - (pi * y) * (pi * y) / 6.0;
+    return std::sin(pi * y) / (pi * y);
+  }
+  return kb_phi(y, H, beta);
+}
+
+double window_s(int kind, double theta, double c, int H, double beta) {
+  const double pi = 3.14159265358979323846;
+  if (kind == 1) return 1.0;
+  double arg = beta * beta - (theta / c) * (theta / c);
+  if (arg <= 0) return 0.0;
+  return 1.0 / (pi * bessel_i0(H * std::sqrt(arg)));
+}
+
 // Solve the (n x n) system A x = b in place (Gaussian elimination, partial pivoting).
 static bool solve(int n, double* A, double* b) {
   for (int c = 0; c < n; ++c) {
@@ -80,10 +102,10 @@ static bool solve(int n, double* A, double* b) {
 // Tap it = t + H - 1 at fraction f = z + 1/2 sits at distance y = f - t.
 // Pair p (0 <= p < H) is tap it = p; its mirror it' = 2H-1-p satisfies
 // w_{it'}(z) = w_p(-z) because phi is even.
-double fit_window(int H, double beta, WindowPoly* out) {
+double fit_window(int kind, int H, double beta, WindowPoly* out) {
   std::memset(out, 0, sizeof(*out));
   const int n = kDeg + 1;
-  const double peak = kb_phi(0.0, H, beta);
+  const double peak = window_phi(kind, 0.0, H, beta);
   const double pi = 3.14159265358979323846;
   double worst = 0.0;
   for (int p = 0; p < H; ++p) {
@@ -93,7 +115,7 @@ double fit_window(int H, double beta, WindowPoly* out) {
       double z = 0.5 * std::cos(pi * (i + 0.5) / n);
       double zp = 1.0;
       for (int d = 0; d < n; ++d) { A[i * n + d] = zp; zp *= z; }
-      b[i] = kb_phi(z + 0.5 - t, H, beta) / peak;
+      b[i] = window_phi(kind, z + 0.5 - t, H, beta) / peak;
     }
     if (!solve(n, A, b)) return 1e30;
     for (int e = 0; e < kHalfCoef; ++e) {
@@ -109,8 +131,8 @@ double fit_window(int H, double beta, WindowPoly* out) {
         O = O * z2 + out->co[p][e];
       }
       double wp = E + z * O, wm = E - z * O;
-      double ep = std::fabs(wp - kb_phi(z + 0.5 - t, H, beta) / peak);
-      double em = std::fabs(wm - kb_phi(-z + 0.5 - t, H, beta) / peak);
+      double ep = std::fabs(wp - window_phi(kind, z + 0.5 - t, H, beta) / peak);
+      double em = std::fabs(wm - window_phi(kind, -z + 0.5 - t, H, beta) / peak);
       if (ep > worst) worst = ep;
       if (em > worst) worst = em;
     }
@@ -118,19 +140,18 @@ double fit_window(int H, double beta, WindowPoly* out) {
   return worst;
 }
 
-double predicted_error(double c, int H, double beta) {
+double predicted_error(int kind, double c, int H, double beta) {
   const double pi = 3.14159265358979323846;
   double worst = 0.0;
   for (int it = 0; it <= 64; ++it) {
     double theta = -pi + 2.0 * pi * it / 64.0;
-    double arg = beta * beta - (theta / c) * (theta / c);
-    if (arg <= 0) return 1.0;
-    double s = 1.0 / (pi * bessel_i0(H * std::sqrt(arg)));
+    double s = window_s(kind, theta, c, H, beta);
+    if (!(s > 0)) return 1.0;
     for (int fi = 0; fi < 32; ++fi) {
       double f = fi / 32.0;
       double re = 0, im = 0;
       for (int t = -H + 1; t <= H; ++t) {
-        double w = kb_phi(f - t, H, beta);
+        double w = window_phi(kind, f - t, H, beta);
         re += w * std::cos(t * theta / c);
         im -= w * std::sin(t * theta / c);
       }
@@ -143,13 +164,12 @@ double predicted_error(double c, int H, double beta) {
   return worst;
 }
 
-void prescale_table(int nt, double c, int H, double beta, double extra, float* out) {
+void prescale_table(int kind, int nt, double c, int H, double beta, double extra, float* out) {
   const double pi = 3.14159265358979323846;
-  const double peak = kb_phi(0.0, H, beta);
+  const double peak = window_phi(kind, 0.0, H, beta);
   for (int n = 0; n < nt; ++n) {
     double theta = 2.0 * pi * n / nt - pi;
-    double arg = beta * beta - (theta / c) * (theta / c);
-    out[n] = (float)(extra * peak / (pi * bessel_i0(H * std::sqrt(arg))));
+    out[n] = (float)(extra * peak * window_s(kind, theta, c, H, beta));
   }
 }
 

@@ -52,6 +52,7 @@ def test_destroy_null_is_ok(pai):
 @pytest.mark.parametrize("field,value", [
     ("dim", 4), ("nx", 7), ("nx", 0), ("nt", 9), ("nz", -2), ("dx", 0.0), ("dt", -1.0), ("c", 0.0),
     ("dz", float("nan")), ("oversampling", 1.0), ("oversampling", 0.5), ("K", -1.0),
+    ("method", 4), ("method", -1),
 ])
 def test_invalid_geometry_rejected_on_host(pai, field, value):
     """Validation happens before any CUDA call, so it is testable without a GPU."""
@@ -60,6 +61,32 @@ def test_invalid_geometry_rejected_on_host(pai, field, value):
     h = ctypes.c_void_p()
     assert pai.load_library().pai_plan(ctypes.byref(g), None, ctypes.byref(h)) == 1
     assert not h.value
+
+
+@pytest.mark.parametrize("method,ok", [(0, False), (1, False), (2, True), (3, True)])
+def test_no_oversampling_only_for_interpolation(pai, method, ok):
+    """c = 1 is valid for the interpolation methods only (Algorithm 1 needs c > 1)."""
+    g = pai.geometry(dict(dim=2, nx=16, nt=32, nz=16, oversampling=1.0, method=method))
+    h = ctypes.c_void_p()
+    lib = pai.load_library()
+    st = lib.pai_plan(ctypes.byref(g), None, ctypes.byref(h))
+    if h.value:
+        lib.pai_destroy(h)
+    assert (st != 1) == ok  # past host validation it succeeds, or fails only for want of a GPU
+
+
+def test_batch_with_mixed_methods_rejected_on_host(pai):
+    gs = (pai.Geometry * 2)(pai.geometry(dict(dim=2, nx=16, nt=32, nz=16)),
+                            pai.geometry(dict(dim=2, nx=16, nt=32, nz=16, method="tsinc")))
+    h = ctypes.c_void_p()
+    assert pai.load_library().pai_plan_batched(gs, 2, None, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_method_names(pai):
+    assert pai.geometry(dict(dim=2, nx=16, nt=32, nz=16, method="nearest")).method == 3
+    with pytest.raises(ValueError):
+        pai.geometry(dict(dim=2, nx=16, nt=32, nz=16, method="cubic"))
 
 
 def test_invalid_pointers_rejected(pai):

@@ -1,0 +1,156 @@
+"""The compared evaluation methods of Sec. 4 on the GPU (libpai through its C
+ABI) against their FP64 oracle (oracle/methods.py).
+
+The method only changes the row kernel's node evaluation: truncated sinc is
+Algorithm 1 with the indicator window (2H = 2 ceil(cK) taps), linear and
+nearest interpolate the unwindowed oversampled DFT.  Bar: relative L2
+<= 1e-5 against the oracle of the SAME method (the methods' own errors against
+the direct reconstruction are percents; they are compared in the Table 1 test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.methods as om
+import phantoms as ph
+from gpu_common import DOT_TOL, TOL, gdict, pai, pipeline, rel, to_gpu, to_np  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _padded(c_req, nt):
+    """The documented padded length: the smallest power of two >= c nt, at least 32."""
+    want = math.ceil(c_req * nt - 1e-9)
+    M = 32
+    while M < want:
+        M *= 2
+    return M
+
+
+def _run(pai, g, p, method, c_req, K=3.0):
+    plan = pai.Plan(gdict(g, method=method, oversampling=c_req, K=K if method == "tsinc" else 0))
+    f = to_np(plan.reconstruct(to_gpu(p)))
+    M = _padded(c_req, g.nt)
+    assert plan.info["M"] == M
+    c = M / g.nt
+    p64 = np.asarray(p, dtype=np.float32).astype(np.float64)
+    if method == "nearest":
+        # the rounding decision must not hinge on the last bits of a node
+        assert om.half_pixel_margin(g, c) > 1e-6
+    K_or = math.ceil(c_req * K - 1e-9) / c  # the kernel's taps span |j - c nu| < ceil(c K)
+    ref = om.reconstruct(g, p64, method, c, K_or)
+    return f, ref, plan
+
+
+METHOD_CASES = [("tsinc", 2.0), ("linear", 2.0), ("nearest", 2.0), ("linear", 1.0), ("nearest", 1.0)]
+
+
+@pytest.mark.parametrize("method,c", METHOD_CASES)
+def test_methods_plain_2d(pai, method, c, pipeline):
+    prob = ph.plain_2d(3)
+    f, ref, plan = _run(pai, prob.geom, prob.p, method, c)
+    if method == "tsinc":
+        assert plan.info["taps"] == 12
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("method,c", METHOD_CASES)
+def test_methods_general_grid_ragged(pai, method, c):
+    """nt not a power of two (c_eff = M/nt != c), nx with a ragged work item,
+    dt != dx, dz != dx, sound speed != 1."""
+    g = ph.Geometry(dim=2, nx=300, nt=700, nz=350, dx=1.0, dt=0.5, c=1.5, dz=0.8)
+    p = ph.random_data(31, g)
+    f, ref, _ = _run(pai, g, p, method, c)
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("method,c", METHOD_CASES)
+def test_methods_3d(pai, method, c, pipeline):
+    g = ph.Geometry(dim=3, nx=64, ny=32, nt=128, nz=64, dy=1.2)
+    p = ph.random_data(32, g)
+    f, ref, _ = _run(pai, g, p, method, c)
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (4, 8, 6), (16, 34, 12)])
+@pytest.mark.parametrize("method", ["tsinc", "linear", "nearest"])
+def test_methods_tiny(pai, shape, method):
+    nx, nt, nz = shape
+    g = ph.Geometry(dim=2, nx=nx, nt=nt, nz=nz, dz=0.93)
+    p = ph.random_data(33, g)
+    f, ref, _ = _run(pai, g, p, method, 2.0)
+    assert rel(f, ref) < TOL
+
+
+def test_methods_batched(pai):
+    """A batch shares the method; each problem keeps its own padded length."""
+    geoms = [ph.Geometry(dim=2, nx=64, nt=130, nz=64, dz=0.9), ph.Geometry(dim=2, nx=36, nt=512, nz=100),
+             ph.Geometry(dim=3, nx=10, ny=8, nt=40, nz=16)]
+    ps = [ph.random_data(40 + i, g) for i, g in enumerate(geoms)]
+    plan = pai.Plan([gdict(g, method="linear", oversampling=2) for g in geoms])
+    out = to_np(plan.reconstruct(to_gpu(np.concatenate([p.ravel() for p in ps]))))
+    off = 0
+    for g, p in zip(geoms, ps):
+        n = g.nx * g.ny * g.nz
+        c = _padded(2.0, g.nt) / g.nt
+        ref = om.reconstruct(g, p.astype(np.float32).astype(np.float64), "linear", c)
+        assert rel(out[off: off + n].reshape(g.image_shape), ref) < TOL
+        off += n
+
+
+def test_mixed_methods_rejected(pai):
+    g = ph.Geometry(dim=2, nx=32, nt=64, nz=32)
+    with pytest.raises(pai.PAIError) as e:
+        pai.Plan([gdict(g), gdict(g, method="linear")])
+    assert e.value.status == 1  # PAI_ERR_INVALID_ARG
+
+
+def test_interpolation_has_no_adjoint(pai):
+    g = ph.Geometry(dim=2, nx=32, nt=64, nz=32)
+    plan = pai.Plan(gdict(g, method="nearest"))
+    with pytest.raises(pai.PAIError) as e:
+        plan.adjoint(to_gpu(ph.random_image(1, g)))
+    assert e.value.status == 2  # PAI_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+                               ph.Geometry(dim=3, nx=32, ny=24, nt=64, nz=32, dz=0.8)],
+                         ids=["2d", "3d"])
+def test_tsinc_adjoint(pai, g, pipeline):
+    """The transposed spread with the sinc window: the dot-product identity
+    between the GPU forward and the GPU adjoint."""
+    plan = pai.Plan(gdict(g, method="tsinc", K=3))
+    p = ph.random_data(80, g)
+    h = ph.random_image(81, g)
+    Rp = to_np(plan.reconstruct(to_gpu(p)))
+    Rth = to_np(plan.adjoint(to_gpu(h)))
+    p32 = p.astype(np.float32).astype(np.float64)
+    h32 = h.astype(np.float32).astype(np.float64)
+    lhs = float(np.vdot(Rp, h32))
+    rhs = float(np.vdot(p32, Rth))
+    assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(Rp) * np.linalg.norm(h32)
+
+
+def test_table1_ordering_on_gpu(pai):
+    """Table 1 from the product path: every method's error against the direct
+    (oracle) reconstruction, in the paper's order, and each equal to its
+    oracle's error up to FP32 rounding."""
+    N = 256
+    pr = ph.fcirc_problem_2d(1, N, 2 * N, N, 3, rmin=N / 32, rmax=N / 8)
+    p64 = pr.p.astype(np.float32).astype(np.float64)
+    ref = oracle.reconstruct(pr.geom, p64)
+    assert om.half_pixel_margin(pr.geom, 1.0) > 1e-6 and om.half_pixel_margin(pr.geom, 2.0) > 1e-6
+    order = [("kb", 2.0), ("tsinc", 2.0), ("linear", 2.0), ("nearest", 2.0), ("linear", 1.0), ("nearest", 1.0)]
+    errs = []
+    for m, c in order:
+        plan = pai.Plan(gdict(pr.geom, method=m, oversampling=c, K=3 if m in ("kb", "tsinc") else 0))
+        f = to_np(plan.reconstruct(to_gpu(pr.p)))
+        e = rel(f, ref)
+        errs.append(e)
+        if m != "kb":
+            e_or = rel(om.reconstruct(pr.geom, p64, m, c, 3.0), ref)
+            assert abs(e - e_or) < 2e-5, (m, c, e, e_or)
+    assert errs[0] < TOL, errs
+    assert all(a < b for a, b in zip(errs, errs[1:])), errs
