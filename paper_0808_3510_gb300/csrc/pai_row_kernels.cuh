@@ -338,14 +338,12 @@ __device__ __forceinline__ void node_position(float2 S, float4 zt, float B2hi, f
   }
 }
 
+// The mirrored node -x = (-j0p - 1) + (1 - frp).  For an integer node fr = 1:
+// the tap polynomials cover z = fr - 1/2 in [-1/2, 1/2] with both ends, and
+// this is the tap set the forward pair evaluation (node_value_pair) uses.
 __device__ __forceinline__ void negate_node(int j0p, float frp, int& j0, float& fr) {
-  if (frp > 0.0f) {
-    j0 = -j0p - 1;
-    fr = 1.0f - frp;
-  } else {
-    j0 = -j0p;
-    fr = 0.0f;
-  }
+  j0 = -j0p - 1;
+  fr = 1.0f - frp;
 }
 
 // e^{+i pi nu} for nu = (j0 + fr) nt / M, returned as (cos, sin).
@@ -481,54 +479,93 @@ __device__ __forceinline__ void node_task(int i, int nzh, int nA, int& lp, bool&
   }
 }
 
+// Values at the node pair +x and -x (x = c nu = j0 + fr, fr in [0, 1)) from one
+// evaluation of the tap polynomials.  The mirrored node is taken as
+// -x = (-j0 - 1) + (1 - fr): its offset z' = (1 - fr) - 1/2 = -z, so its tap q
+// weighs w_q(-z) = w_{2H-1-q}(z) (phi is even), and its phase
+// e^{-i pi (-nu)} is the conjugate of the phase of +x.  Both values come out
+// exactly as node_eval would give them for the two nodes, without rounding
+// 1 - fr.
+template <int H>
+__device__ __forceinline__ void node_value_pair(const RowProblem& P, const float2* U, const WindowPoly& W, int j0,
+                                                float fr, float2& vp, float2& vn) {
+  if constexpr (H == 2) {
+    if (P.method >= PAI_METHOD_LINEAR) {
+      vp = node_interp(U, P.method, j0, fr, P.M, P.nt, P.nt_over_M);
+      vn = node_interp(U, P.method, -j0 - 1, 1.0f - fr, P.M, P.nt, P.nt_over_M);
+      return;
+    }
+  }
+  const int mask = P.M - 1;
+  const float2* gp = U + ((j0 - H + 1) & mask);
+  const float2* gn = U + ((-j0 - H) & mask);
+  const float z = fr - 0.5f, z2 = z * z;
+  float ax = 0.0f, ay = 0.0f, bx = 0.0f, by = 0.0f;
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+    for (int e = kHalfCoef - 2; e >= 0; --e) {
+      E = fmaf(E, z2, W.ce[p][e]);
+      O = fmaf(O, z2, W.co[p][e]);
+    }
+    const float wl = fmaf(z, O, E), wh = fmaf(-z, O, E);
+    const float2 pl = gp[p], ph = gp[2 * H - 1 - p];
+    const float2 nl = gn[p], nh = gn[2 * H - 1 - p];
+    ax = fmaf(wl, pl.x, ax);
+    ay = fmaf(wl, pl.y, ay);
+    ax = fmaf(wh, ph.x, ax);
+    ay = fmaf(wh, ph.y, ay);
+    bx = fmaf(wh, nl.x, bx);
+    by = fmaf(wh, nl.y, by);
+    bx = fmaf(wl, nh.x, bx);
+    by = fmaf(wl, nh.y, by);
+  }
+  const float2 ph = node_phase(j0, fr, P.nt, P.M, P.nt_over_M);
+  vp = make_float2(fmaf(ax, ph.x, ay * ph.y), fmaf(ay, ph.x, -ax * ph.y));
+  vn = make_float2(fmaf(bx, ph.x, -by * ph.y), fmaf(by, ph.x, bx * ph.y));
+}
+
+// Half image spectrum of one row (ZF = false layout): for l' = 1 .. nz/2 one
+// task evaluates the node pair +-|K|; destination row d1 takes the +nu value,
+// the conjugate row d2 (mirror rows only) the conjugate of the -nu value, and
+// the Nyquist entry l' = nz/2 the mean of both (reading of the l = -nz/2 row).
+// Self-conjugate rows (no mirror) need the -nu value only at the Nyquist entry.
 template <int H>
 __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly& W, const float2* X, int row,
                                            int lane) {
   const RowGeom rg = row_geom(P, row);
   const int nzh = P.nz >> 1;
-  const int nA = rg.mirror ? (P.nz - 1) : nzh;
   float2* out1 = P.fh + (size_t)rg.d1 * P.lz;
   float2* out2 = P.fh + (size_t)rg.d2 * P.lz;
   if (lane == 0) {
     out1[0] = make_float2(0.f, 0.f);
     if (rg.mirror) out2[0] = make_float2(0.f, 0.f);
   }
-  // the depth-table entry of the next node is loaded one iteration ahead
-  int lp_next = 0;
-  {
-    bool n_, y_;
-    if (lane < nA) node_task(lane, nzh, nA, lp_next, n_, y_);
-  }
-  float4 zt_next = __ldg(&P.zt[lp_next]);
-  for (int i = lane; i < nA; i += P.tpr) {
-    int lp;
-    bool neg, nyq;
-    node_task(i, nzh, nA, lp, neg, nyq);
+  // the depth-table entry of the next task is loaded one iteration ahead
+  float4 zt_next = __ldg(&P.zt[min(lane, nzh - 1) + 1]);
+  for (int i = lane; i < nzh; i += P.tpr) {
+    const int lp = i + 1;
     const float4 zt = zt_next;
-    if (i + P.tpr < nA) {
-      bool n_, y_;
-      node_task(i + P.tpr, nzh, nA, lp_next, n_, y_);
-      zt_next = __ldg(&P.zt[lp_next]);
-    }
-    int j0p, j0;
-    float frp, fr, x0;
-    node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+    if (i + P.tpr < nzh) zt_next = __ldg(&P.zt[lp + P.tpr]);
+    int j0;
+    float fr, x0;
+    node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, x0);
     const float wt = P.wscale * zt.z / x0;
-    if (!neg) {
-      float2 v = node_eval<H>(P, X, W, j0p, frp);
-      if (nyq) {
-        negate_node(j0p, frp, j0, fr);
-        float2 u = node_eval<H>(P, X, W, j0, fr);
-        float2 a = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
+    if (lp == nzh || rg.mirror) {
+      float2 v, u;
+      node_value_pair<H>(P, X, W, j0, fr, v, u);
+      if (lp == nzh) {
+        const float2 a = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
         out1[lp] = a;
         if (rg.mirror) out2[lp] = make_float2(a.x, -a.y);
       } else {
         out1[lp] = make_float2(wt * v.x, wt * v.y);
+        out2[lp] = make_float2(wt * u.x, -wt * u.y);
       }
     } else {
-      negate_node(j0p, frp, j0, fr);
-      float2 u = node_eval<H>(P, X, W, j0, fr);
-      out2[lp] = make_float2(wt * u.x, -wt * u.y);
+      const float2 v = node_eval<H>(P, X, W, j0, fr);
+      out1[lp] = make_float2(wt * v.x, wt * v.y);
     }
   }
 }
@@ -537,47 +574,29 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
 // [-nz/2, nz/2), stored at Zs[l mod nz] (Zs = the row's line of the output),
 // from the row's nodes at +nu (l > 0) and -nu (l < 0):  F[l] = W P(sign(l)|K|)
 // for 0 < |l| < nz/2, F[0] = 0 (l = 0 rule), F[-nz/2] = W (P(+|K|) + P(-|K|))/2
-// (Nyquist rule).  An inverse depth FFT of each line followed by the lateral
-// C2R completes Eq. (fft-1).
+// (Nyquist rule).  One task per |l| evaluates the node pair.  An inverse depth
+// FFT of each line followed by the lateral C2R completes Eq. (fft-1).
 template <int H>
 __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPoly& W, const float2* X, float2* Zs,
                                              int row, int lane) {
   const float2 S = P.rowS[row];
   const int nzh = P.nz >> 1;
-  const int nA = P.nz - 1;
   if (lane == 0) Zs[0] = make_float2(0.f, 0.f);
-  int lp_next = 0;
-  {
-    bool n_, y_;
-    if (lane < nA) node_task(lane, nzh, nA, lp_next, n_, y_);
-  }
-  float4 zt_next = __ldg(&P.zt[lp_next]);
-  for (int i = lane; i < nA; i += P.tpr) {
-    int lp;
-    bool neg, nyq;
-    node_task(i, nzh, nA, lp, neg, nyq);
+  float4 zt_next = __ldg(&P.zt[min(lane, nzh - 1) + 1]);
+  for (int i = lane; i < nzh; i += P.tpr) {
+    const int lp = i + 1;
     const float4 zt = zt_next;
-    if (i + P.tpr < nA) {
-      bool n_, y_;
-      node_task(i + P.tpr, nzh, nA, lp_next, n_, y_);
-      zt_next = __ldg(&P.zt[lp_next]);
-    }
-    int j0p, j0;
-    float frp, fr, x0;
-    node_position(S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+    if (i + P.tpr < nzh) zt_next = __ldg(&P.zt[lp + P.tpr]);
+    int j0;
+    float fr, x0;
+    node_position(S, zt, P.B2hi, P.B2lo, j0, fr, x0);
     const float wt = P.wscale * zt.z / x0;
-    if (!neg) {
-      const float2 v = node_eval<H>(P, X, W, j0p, frp);
-      if (nyq) {
-        negate_node(j0p, frp, j0, fr);
-        const float2 u = node_eval<H>(P, X, W, j0, fr);
-        Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
-      } else {
-        Zs[lp] = make_float2(wt * v.x, wt * v.y);
-      }
+    float2 v, u;
+    node_value_pair<H>(P, X, W, j0, fr, v, u);
+    if (lp == nzh) {
+      Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
     } else {
-      negate_node(j0p, frp, j0, fr);
-      const float2 u = node_eval<H>(P, X, W, j0, fr);
+      Zs[lp] = make_float2(wt * v.x, wt * v.y);
       Zs[P.nz - lp] = make_float2(wt * u.x, wt * u.y);
     }
   }
