@@ -26,6 +26,17 @@ __host__ __device__ inline int lateral_slot(int L) { return L + (L >> 5) + 4; }
 
 enum : int { kLatR2C = 0, kLatC2R = 1, kLatC2C = 2, kLatC2CInv = 3 };
 
+// The values a thread loads, column elements x0 + i L/16 (i = 0..15), are the
+// inputs of butterfly x0 of the first radix-16 Stockham pass (Ns = 1): that
+// pass runs on them in registers and writes its outputs 16 x0 + r in the
+// padded layout, ready for fft_rest.
+template <bool INV>
+__device__ __forceinline__ void first_pass_regs(float2* Z, float2 (&z)[kElemsPerThread], int x0) {
+  dft_reg<kElemsPerThread, INV>(z);
+#pragma unroll
+  for (int r = 0; r < kElemsPerThread; ++r) Z[PADI(x0 * kElemsPerThread + r)] = z[r];
+}
+
 template <int KIND, int FP>
 __global__ void __launch_bounds__(1024) lateral_kernel(const void* vin, void* vout, int L,
                                                        int mshift, int C, long long in_outer, long long out_outer,
@@ -54,8 +65,7 @@ __global__ void __launch_bounds__(1024) lateral_kernel(const void* vin, void* vo
 #pragma unroll
     for (int i = 0; i < kElemsPerThread; ++i)
       z[i] = live ? __ldg(src + (size_t)i * xs * (C / 2)) : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < kElemsPerThread; ++i) Z[PADI(x0 + i * xs)] = z[i];
+    first_pass_regs<false>(Z, z, x0);
   } else if (KIND == kLatC2C || KIND == kLatC2CInv) {
     const float2* in = static_cast<const float2*>(vin) + ob * in_outer;
     const bool live = c0 + f < C;
@@ -64,8 +74,7 @@ __global__ void __launch_bounds__(1024) lateral_kernel(const void* vin, void* vo
 #pragma unroll
     for (int i = 0; i < kElemsPerThread; ++i)  // plain loads: the C2C may run in place
       z[i] = live ? src[(size_t)i * xs * C] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < kElemsPerThread; ++i) Z[PADI(x0 + i * xs)] = z[i];
+    first_pass_regs<kInv>(Z, z, x0);
   } else {  // C2R: rows k = 0 .. L/2 of two complex columns per slot
     const float2* in = static_cast<const float2*>(vin) + ob * in_outer;
     const bool live = c0 + 2 * f < C;
@@ -97,7 +106,8 @@ __global__ void __launch_bounds__(1024) lateral_kernel(const void* vin, void* vo
   {
     const int slot = threadIdx.x / tpr;
     const int lane = threadIdx.x - slot * tpr;
-    fft_smem<kInv, kLayoutFlat>(smem + slot * S, L, mshift, lane, tpr, tw, twstride);
+    if (KIND == kLatC2R) fft_smem<kInv, kLayoutFlat>(smem + slot * S, L, mshift, lane, tpr, tw, twstride);
+    else fft_rest<kInv, kLayoutFlat>(smem + slot * S, L, mshift, lane, tpr, tw, twstride);
   }
 
   // ---- store ------------------------------------------------------------
