@@ -186,6 +186,11 @@ __device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
   }
 }
 
+// Padded addresses without per-element shifts: for a multiple S of 32,
+// PADI(a + r S) = PADI(a) + r (S + S/32); and for a with a mod 32 < 16,
+// PADI(a + 16 r) = PADI(a) + 16 r + r/2 (r < 16).  Both hold for every pass
+// after the first radix-16 one (Ns = 16 or a multiple of 256), and for the
+// first pass (Ns = 1) PADI(16 j + r) = PADI(16 j) + r.
 template <int R, bool INV, int OUT>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
                                          int twstride, bool active = true) {
@@ -199,13 +204,20 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
   // several butterflies per thread and load after it to stay within registers
   if (active) {
     if (Ns > 1 && NB == 1) tw_load<R>(t[0], tw, (lane & (Ns - 1)) * tws);
+    if ((MR & 31) == 0) {
+      const int rs = MR + (MR >> 5);
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const int j = lane + i * tpr;
+      for (int i = 0; i < NB; ++i) {
+        const float2* src = X + PADI(lane + i * tpr);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int idx = j + r * MR;
-        v[i][r] = X[PADI(idx)];
+        for (int r = 0; r < R; ++r) v[i][r] = src[r * rs];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const int j = lane + i * tpr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i][r] = X[PADI(j + r * MR)];
       }
     }
   }
@@ -221,14 +233,30 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
     }
     dft_reg<R, INV>(v[i]);
     const int base = (j - k) * R + k;
+    if (OUT == kLayoutPadded) {
+      float2* dst = X + PADI(base);
+      if (Ns == 16) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int idx = base + r * Ns;
-      if (OUT == kLayoutPadded) {
-        X[PADI(idx)] = v[i][r];
+        for (int r = 0; r < R; ++r) dst[16 * r + (r >> 1)] = v[i][r];
+      } else if ((Ns & 31) == 0) {
+        const int ws = Ns + (Ns >> 5);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r * ws] = v[i][r];
+      } else if (Ns == 1 && R == 16) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r] = v[i][r];
       } else {
-        X[idx] = v[i][r];
-        if (OUT == kLayoutFlatGhost && idx < 2 * kMaxH) X[M + idx] = v[i][r];
+#pragma unroll
+        for (int r = 0; r < R; ++r) X[PADI(base + r * Ns)] = v[i][r];
+      }
+    } else {
+      float2* dst = X + base;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * Ns] = v[i][r];
+      if (OUT == kLayoutFlatGhost && base < 2 * kMaxH) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (base + r * Ns < 2 * kMaxH) X[M + base + r * Ns] = v[i][r];
       }
     }
   }
@@ -259,11 +287,9 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
     v[r] = a;
   }
   dft_reg<R, false>(v);
+  float2* dst = X + PADI(lane * R);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int idx = lane * R + r;
-    X[PADI(idx)] = v[r];
-  }
+  for (int r = 0; r < R; ++r) dst[r] = v[r];
   __syncthreads();
 }
 
