@@ -101,7 +101,8 @@ typedef struct {
 typedef struct {
   int count;              /* problems in the plan (1 unless batched)            */
   int M;                  /* padded temporal FFT length of problem 0            */
-  int taps;               /* taps per node (2*ceil(c_os*K))                      */
+  int taps;               /* grid values read per node: 2*ceil(c_os*K) for the
+                             windowed methods, 2 (linear), 1 (nearest)          */
   double oversampling;    /* effective c_os = M/nt of problem 0                  */
   double K, alpha;        /* effective window parameters of problem 0 (alpha is
                              0 and K the tap half-width for the truncated sinc;

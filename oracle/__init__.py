@@ -96,6 +96,8 @@ def _load():
         lib.oracle_reconstruct.restype = i
         lib.oracle_adjoint.argtypes = [G, dp, dp, i]
         lib.oracle_adjoint.restype = i
+        lib.oracle_adjoint_box.argtypes = [G, dp, i, i, i, i, i, i, dp, i]
+        lib.oracle_adjoint_box.restype = i
         lib.oracle_threads.argtypes = [i]
         lib.oracle_threads.restype = i
         _lib = lib
@@ -251,3 +253,22 @@ def adjoint(g, h: np.ndarray, nthreads: int = 0) -> np.ndarray:
     if _load().oracle_adjoint(ctypes.byref(gg), _dptr(a), _dptr(out), nthreads):
         raise MemoryError("oracle_adjoint failed")
     return out.reshape(_out_shape(gg, gg.nt))
+
+
+def adjoint_box(g, h: np.ndarray, x, y, n, nthreads: int = 0) -> np.ndarray:
+    """:func:`adjoint` evaluated only on the box of output samples x = range(*x),
+    y = range(*y) (ignored in 2-D), n = range(*n), each a (start, stop) pair;
+    for grids whose full adjoint is too costly to form directly."""
+    gg = _geom(g)
+    a = np.ascontiguousarray(h, dtype=np.float64)
+    if a.size != gg.nx * gg.ny * gg.nz:
+        raise ValueError("image size does not match the geometry")
+    y = (0, 1) if gg.dim == 2 else y
+    cx, cy, cn = x[1] - x[0], y[1] - y[0], n[1] - n[0]
+    out = np.empty((cx, cy, cn), np.float64)
+    rc = _load().oracle_adjoint_box(ctypes.byref(gg), _dptr(a), x[0], cx, y[0], cy, n[0], cn, _dptr(out), nthreads)
+    if rc == -2:
+        raise ValueError("box outside the data grid")
+    if rc:
+        raise MemoryError("oracle_adjoint_box failed")
+    return out.reshape((cx, cn)) if gg.dim == 2 else out

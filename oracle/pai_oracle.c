@@ -580,4 +580,105 @@ int oracle_adjoint(const oracle_geom* g, const double* h, double* pbar, int thre
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* The adjoint on a box of output samples (large grids)                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const oracle_geom* g; const cplx* F; cplx* q; int n0, cn;
+} box_row_ctx;
+
+/* q[row][n'] = sum_l e^{+i 2 pi nu (n0 + n') / nt} W F[row][l], n' < cn */
+static void box_row(void* a, long row) {
+  box_row_ctx* c = (box_row_ctx*)a;
+  const oracle_geom* g = c->g;
+  int kx = signed_freq((int)(row / g->ny), g->nx);
+  int ky = signed_freq((int)(row % g->ny), g->ny);
+  for (int j = 0; j < c->cn; ++j) c->q[(size_t)row * c->cn + j] = 0;
+  for (int li = 0; li < g->nz; ++li) {
+    int l = signed_freq(li, g->nz);
+    double nu = oracle_node(g, kx, ky, l);
+    cplx h = oracle_weight(g, kx, ky, l) * c->F[(size_t)row * g->nz + li];
+    for (int j = 0; j < c->cn; ++j) {
+      double turns = nu * (double)(c->n0 + j) / (double)g->nt;
+      turns -= floor(turns);
+      double ang = TWO_PI * turns;
+      c->q[(size_t)row * c->cn + j] += (cos(ang) + I * sin(ang)) * h;
+    }
+  }
+}
+
+typedef struct {
+  const oracle_geom* g; const cplx* q; const cplx* wx; const cplx* wy;
+  int x0, y0, cy, cn; double* out;
+} box_lat_ctx;
+
+/* out[x'][y'][n'] = Re sum_{kx,ky} e^{+2 pi i (kx x/nx + ky y/ny)} q[kx][ky][n'] */
+static void box_lat(void* a, long xi) {
+  box_lat_ctx* c = (box_lat_ctx*)a;
+  const oracle_geom* g = c->g;
+  int x = c->x0 + (int)xi;
+  cplx* acc = (cplx*)calloc((size_t)c->cy * c->cn, sizeof(cplx));
+  for (int ki = 0; ki < g->nx; ++ki) {
+    int kx = signed_freq(ki, g->nx);
+    long mx = ((long)kx * x) % g->nx; if (mx < 0) mx += g->nx;
+    cplx wxv = conj(c->wx[mx]);
+    for (int kj = 0; kj < g->ny; ++kj) {
+      int ky = signed_freq(kj, g->ny);
+      const cplx* src = c->q + ((size_t)ki * g->ny + kj) * c->cn;
+      for (int yi = 0; yi < c->cy; ++yi) {
+        int y = c->y0 + yi;
+        long my = ((long)ky * y) % g->ny; if (my < 0) my += g->ny;
+        cplx w = wxv * conj(c->wy[my]);
+        cplx* d = acc + (size_t)yi * c->cn;
+        for (int j = 0; j < c->cn; ++j) d[j] += w * src[j];
+      }
+    }
+  }
+  for (size_t i = 0; i < (size_t)c->cy * c->cn; ++i) c->out[(size_t)xi * c->cy * c->cn + i] = creal(acc[i]);
+  free(acc);
+}
+
+/* The adjoint of oracle_reconstruct restricted to the output box
+ * x in [x0, x0+cx), y in [y0, y0+cy) (y0 = 0, cy = 1 in 2-D), n in [n0, n0+cn):
+ * out[x'][y'][n'] = pbar[x0+x'][y0+y'][n0+n'] with the same sums as
+ * oracle_adjoint (image-side DFT in full, the temporal and lateral adjoint sums
+ * only at the requested samples). */
+int oracle_adjoint_box(const oracle_geom* g, const double* h, int x0, int cx, int y0, int cy, int n0, int cn,
+                       double* out, int threads) {
+  if (x0 < 0 || cx < 1 || x0 + cx > g->nx || y0 < 0 || cy < 1 || y0 + cy > g->ny || n0 < 0 || cn < 1 ||
+      n0 + cn > g->nt)
+    return -2;
+  size_t rows = (size_t)g->nx * g->ny;
+  size_t nimg = rows * g->nz;
+  cplx* a = (cplx*)malloc(sizeof(cplx) * nimg);
+  cplx* b = (cplx*)malloc(sizeof(cplx) * nimg);
+  cplx* q = (cplx*)malloc(sizeof(cplx) * rows * (size_t)cn);
+  cplx* wz = twiddle_table(g->nz);
+  cplx* wx = twiddle_table(g->nx);
+  cplx* wy = twiddle_table(g->ny);
+  if (!a || !b || !q || !wz || !wx || !wy) {
+    free(a); free(b); free(q); free(wz); free(wx); free(wy);
+    return -1;
+  }
+  fz_ctx cz = {g, h, a, wz};
+  parallel_rows(fwd_z_row, &cz, (long)rows, threads);
+  fl_ctx cxx = {g, a, b, wx, g->nz};
+  parallel_rows(fwd_x_row, &cxx, g->nx, threads);
+  cplx* F = b;
+  if (g->dim == 3) {
+    fl_ctx cy_ = {g, b, a, wy, g->nz};
+    parallel_rows(fwd_y_row, &cy_, g->nx, threads);
+    F = a;
+  }
+  double scale = 1.0 / ((double)g->nx * g->ny * g->nz);
+  for (size_t i = 0; i < nimg; ++i) F[i] *= scale;
+  box_row_ctx cr = {g, F, q, n0, cn};
+  parallel_rows(box_row, &cr, (long)rows, threads);
+  box_lat_ctx cl = {g, q, wx, wy, x0, y0, cy, cn, out};
+  parallel_rows(box_lat, &cl, cx, threads);
+  free(a); free(b); free(q); free(wz); free(wx); free(wy);
+  return 0;
+}
+
 int oracle_threads(int requested) { return n_threads(requested); }

@@ -939,7 +939,7 @@ pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info) {
   const ProblemHost& p = plan->probs[0];
   info->count = (int)plan->probs.size();
   info->M = p.M;
-  info->taps = 2 * plan->H;
+  info->taps = plan->method == PAI_METHOD_LINEAR ? 2 : plan->method == PAI_METHOD_NEAREST ? 1 : 2 * plan->H;
   info->oversampling = p.c_eff;
   info->K = p.K_eff;
   info->alpha = p.alpha_eff;

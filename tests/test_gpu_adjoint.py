@@ -107,3 +107,47 @@ def test_finite_differences(pai, step, tol):
         fd.append(np.dot(d, 0.5 * (ra + rb) - f_true.ravel()) / (2 * step))
     fd = np.array(fd)
     assert rel(fd, grad[idx]) < tol
+
+
+def test_adjoint_3d_full_size(pai):
+    """The 3-D adjoint workload at full size (256 x 256 detectors x 512 samples
+    -> 256^3, c = 2, K = 3, the benchmark's gradient step): the gradient of
+    0.5 ||R p - f||^2 through PAIRecon against the oracle's adjoint of the same
+    residual on a 32 x 32 x 32 box of detector samples, the dot-product
+    identity, and the directional derivative along 32 coordinates e_i.  R is
+    linear, so the central difference (R(p + h e_i) - R(p - h e_i)) / 2h is R e_i
+    for every step h; it is formed as R e_i directly, which keeps FP32 rounding
+    of R p out of the difference."""
+    import torch
+    prob = ph.adjoint_3d(0)
+    g = prob.geom
+    plan = pai.Plan(gdict(g, oversampling=2, K=3))
+    p0 = prob.p.astype(np.float32)
+    f_true = ph.random_image(74, g).astype(np.float32)
+    pt = to_gpu(p0).requires_grad_(True)
+    ft = to_gpu(f_true)
+    loss = 0.5 * ((pai.PAIRecon.apply(pt, plan) - ft) ** 2).sum()
+    loss.backward()
+    grad = to_np(pt.grad)
+    with torch.no_grad():
+        resid = to_np(plan.reconstruct(pt.detach()) - ft)
+    box = ((112, 144), (112, 144), (240, 272))
+    ref = oracle.adjoint_box(g, resid, *box)
+    assert rel(grad[112:144, 112:144, 240:272], ref) < TOL
+    # dot product identity at full size
+    h = ph.random_image(75, g).astype(np.float32)
+    Rp = to_np(plan.reconstruct(to_gpu(p0)))
+    Rth = to_np(plan.adjoint(to_gpu(h)))
+    lhs = float(np.vdot(Rp, h.astype(np.float64)))
+    rhs = float(np.vdot(p0.astype(np.float64), Rth))
+    assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(Rp) * np.linalg.norm(h)
+    # directional derivatives along 32 coordinates (seed 0)
+    idx = np.random.default_rng(0).choice(p0.size, 32, replace=False)
+    e = torch.zeros(p0.size, device="cuda", dtype=torch.float32)
+    dd = []
+    for i in idx:
+        e.zero_()
+        e[int(i)] = 1.0
+        Re = to_np(plan.reconstruct(e.view(g.data_shape))).ravel()
+        dd.append(float(np.dot(Re, resid.ravel())))
+    assert rel(np.array(dd), grad.ravel()[idx]) < 1e-5

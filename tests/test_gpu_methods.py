@@ -154,3 +154,52 @@ def test_table1_ordering_on_gpu(pai):
             assert abs(e - e_or) < 2e-5, (m, c, e, e_or)
     assert errs[0] < TOL, errs
     assert all(a < b for a, b in zip(errs, errs[1:])), errs
+
+
+def test_fig5_time_versus_error(pai):
+    """Fig. 5: reconstruction time against error for oversampling factors
+    c in {1, 2, 4, 8, 16, 32} (Kaiser-Bessel from c = 2, its interpolation
+    length from the plan's truncation-error rule).  The interpolation errors
+    fall as c grows; the Kaiser-Bessel error stays at the FP32 floor for every
+    c, below the best interpolation error.  The table is printed, and written
+    to the file named by PAI_FIG5_OUT when that is set."""
+    import json
+    import os
+
+    import torch
+    N = 256
+    pr = ph.fcirc_problem_2d(1, N, 2 * N, N, 3, rmin=N / 32, rmax=N / 8)
+    p64 = pr.p.astype(np.float32).astype(np.float64)
+    ref = oracle.reconstruct(pr.geom, p64)
+    x = to_gpu(pr.p)
+    rows = []
+    for m in ("nearest", "linear", "kb"):
+        for c in (1, 2, 4, 8, 16, 32):
+            if m == "kb" and c == 1:
+                continue
+            plan = pai.Plan(gdict(pr.geom, method=m, oversampling=float(c)))
+            out = plan.reconstruct(x)
+            for _ in range(3):
+                plan.reconstruct(x, out=out)
+            s = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(20):
+                plan.reconstruct(x, out=out)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+            err = rel(to_np(out), ref)
+            rows.append({"method": m, "c": c, "M": plan.info["M"], "taps": plan.info["taps"], "ms": ms,
+                         "rel_l2_vs_direct": err})
+            plan.close()
+    print(json.dumps(rows, indent=1))
+    if os.environ.get("PAI_FIG5_OUT"):
+        with open(os.environ["PAI_FIG5_OUT"], "w") as fh:
+            json.dump(rows, fh, indent=1)
+    by = {(r["method"], r["c"]): r["rel_l2_vs_direct"] for r in rows}
+    for m in ("nearest", "linear"):
+        errs = [by[(m, c)] for c in (1, 2, 4, 8, 16, 32)]
+        assert all(a > b for a, b in zip(errs, errs[1:])), (m, errs)
+    kb = [by[("kb", c)] for c in (2, 4, 8, 16, 32)]
+    assert max(kb) < TOL and max(kb) < by[("linear", 32)], kb

@@ -345,3 +345,22 @@ def test_algorithm1_within_paper_bound_of_oracle(alpha_over_pi, limit):
     exact = oracle.nudft(g, nu)
     approx = _nufft_fp64(g, nu, 2.0, 3.0, alpha_over_pi * np.pi)
     assert _rel(approx, exact) < limit
+
+
+@pytest.mark.parametrize("g,box", [
+    (ph.Geometry(dim=3, nx=12, ny=10, nt=20, nz=8, dx=0.9, dy=1.1, dt=0.7, c=1.3, dz=1.2), ((3, 9), (0, 10), (5, 17))),
+    (ph.Geometry(dim=2, nx=14, nt=24, nz=10, dt=0.8, dz=1.1), ((0, 14), None, (0, 24))),
+    (ph.Geometry(dim=2, nx=14, nt=24, nz=10), ((5, 6), None, (23, 24))),
+])
+def test_adjoint_box_is_the_adjoint_restricted(g, box):
+    """The box-restricted adjoint (for grids too large for the full one) is
+    the full oracle adjoint on that box, sample for sample."""
+    h = np.random.default_rng(9).standard_normal(g.image_shape)
+    full = oracle.adjoint(g, h)
+    bx, by, bn = box
+    got = oracle.adjoint_box(g, h, bx, by, bn)
+    if g.dim == 2:
+        ref = full[bx[0]:bx[1], bn[0]:bn[1]]
+    else:
+        ref = full[bx[0]:bx[1], by[0]:by[1], bn[0]:bn[1]]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(full))
