@@ -174,6 +174,22 @@ pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat);
  * plan-owned device staging buffers allocated on first use.                  */
 pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f);
 
+/* The same, pipelined across calls (a stream of reconstructions from host
+ * memory, e.g. successive frames): returns once the work is enqueued.  The
+ * copy of this call's h_p to the device, its reconstruction and the copy of
+ * its image into h_f run on three streams with two plan-owned device staging
+ * pairs (allocated on first use), so one call's upload overlaps the previous
+ * call's transforms and the download of the one before.  h_p and h_f must be
+ * page-locked for the copies to be asynchronous (pageable memory still works,
+ * but its copies block the caller).  The caller must not modify h_p nor read
+ * h_f until pai_host_wait returns.  Not a paper operation: a transfer
+ * schedule around pai_reconstruct.                                           */
+pai_status pai_reconstruct_host_async(pai_plan_t plan, const float* h_p, float* h_f);
+
+/* Block until every pai_reconstruct_host_async call on the plan has finished
+ * (images in their h_f).                                                     */
+pai_status pai_host_wait(pai_plan_t plan);
+
 /* Per-stage device times for profiling.  Runs `reps` eager (not graph)
  * passes of pai_reconstruct (adjoint = 0) or pai_adjoint (adjoint = 1) on the
  * given device buffers with CUDA events between the stages, synchronises the

@@ -111,9 +111,12 @@ def load_library() -> ctypes.CDLL:
         lib.pai_plan.restype = st
         lib.pai_plan_batched.argtypes = [G, ctypes.c_int, vp, ctypes.POINTER(vp)]
         lib.pai_plan_batched.restype = st
-        for name in ("pai_reconstruct", "pai_adjoint", "pai_spectrum", "pai_reconstruct_host"):
+        for name in ("pai_reconstruct", "pai_adjoint", "pai_spectrum", "pai_reconstruct_host",
+                     "pai_reconstruct_host_async"):
             getattr(lib, name).argtypes = [vp, fp, fp]
             getattr(lib, name).restype = st
+        lib.pai_host_wait.argtypes = [vp]
+        lib.pai_host_wait.restype = st
         lib.pai_profile_stages.argtypes = [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.pai_profile_stages.restype = st
         lib.pai_set_stream.argtypes = [vp, vp]
@@ -305,6 +308,22 @@ class Plan:
         _check(self._lib.pai_reconstruct_host(self._h, ctypes.c_void_p(p_host.data_ptr()),
                                               ctypes.c_void_p(out.data_ptr())), "pai_reconstruct_host")
         return out
+
+    def reconstruct_host_async(self, p_host: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        """Pipelined end-to-end call (pai_reconstruct_host_async): enqueues the upload,
+        the reconstruction and the download, and returns at once.  Neither tensor may be
+        touched until :meth:`host_wait` returns; use page-locked tensors."""
+        for t, n, what in ((p_host, self.data_numel, "p_host"), (out, self.image_numel, "out")):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{what} must be a contiguous float32 CPU tensor with {n} elements")
+        self._sync_stream()
+        _check(self._lib.pai_reconstruct_host_async(self._h, ctypes.c_void_p(p_host.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr())), "pai_reconstruct_host_async")
+        return out
+
+    def host_wait(self):
+        """Wait for every :meth:`reconstruct_host_async` call of this plan."""
+        _check(self._lib.pai_host_wait(self._h), "pai_host_wait")
 
     def profile_stages(self, x: torch.Tensor, out: torch.Tensor, reps: int = 10, adjoint: bool = False):
         """Mean device milliseconds per pass of (first FFT stage, row kernel, last FFT stage)."""

@@ -95,6 +95,12 @@ struct pai_plan_s {
   // host staging for pai_reconstruct_host
   float* d_stage_in = nullptr;
   float* d_stage_out = nullptr;
+  // pipelined host calls: two staging pairs, upload / download streams
+  float* d_pipe_in[2] = {nullptr, nullptr};
+  float* d_pipe_out[2] = {nullptr, nullptr};
+  cudaStream_t s_up = nullptr, s_down = nullptr;
+  cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+  long long host_calls = 0;
   bool use_graph = true;
   std::vector<GraphEntry> graphs;
   long long own_kernels = 0, fft_execs = 0;
@@ -196,6 +202,17 @@ void release(pai_plan_s* P) {
   cudaGetDevice(&prev);
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
+  if (P->s_up) cudaStreamSynchronize(P->s_up);
+  if (P->s_down) cudaStreamSynchronize(P->s_down);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(P->d_pipe_in[k]);
+    cudaFree(P->d_pipe_out[k]);
+    if (P->ev_up[k]) cudaEventDestroy(P->ev_up[k]);
+    if (P->ev_comp[k]) cudaEventDestroy(P->ev_comp[k]);
+    if (P->ev_down[k]) cudaEventDestroy(P->ev_down[k]);
+  }
+  if (P->s_up) cudaStreamDestroy(P->s_up);
+  if (P->s_down) cudaStreamDestroy(P->s_down);
   for (auto& ge : P->graphs)
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
   for (auto& p : P->probs) destroy_fft(p);
@@ -883,6 +900,62 @@ pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
   if (st == PAI_OK)
     st = cuda_status(cudaMemcpyAsync(h_f, plan->d_stage_out, plan->img_total * sizeof(float),
                                      cudaMemcpyDeviceToHost, plan->stream));
+  if (st == PAI_OK) st = cuda_status(cudaStreamSynchronize(plan->stream));
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+// Call k uses staging pair k mod 2.  Upload stream: wait until call k-2's
+// transforms have read d_pipe_in (ev_comp), copy in, record ev_up.  Plan
+// stream: wait for the upload and for call k-2's download of d_pipe_out
+// (ev_down), run the graph, record ev_comp.  Download stream: wait for the
+// transforms, copy out, record ev_down.
+pai_status pai_reconstruct_host_async(pai_plan_t plan, const float* h_p, float* h_f) {
+  if (!plan || !h_p || !h_f) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = PAI_OK;
+  if (!plan->s_up) {
+    st = cuda_status(cudaStreamCreateWithFlags(&plan->s_up, cudaStreamNonBlocking));
+    if (st == PAI_OK) st = cuda_status(cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking));
+    for (int k = 0; k < 2 && st == PAI_OK; ++k) {
+      st = cuda_status(cudaMalloc(&plan->d_pipe_in[k], plan->data_total * sizeof(float)));
+      if (st == PAI_OK) st = cuda_status(cudaMalloc(&plan->d_pipe_out[k], plan->img_total * sizeof(float)));
+      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_up[k], cudaEventDisableTiming));
+      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_comp[k], cudaEventDisableTiming));
+      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_down[k], cudaEventDisableTiming));
+    }
+  }
+  const int k = (int)(plan->host_calls & 1);
+  const bool reuse = plan->host_calls >= 2;  // events of call k-2 exist
+  if (st == PAI_OK && reuse) st = cuda_status(cudaStreamWaitEvent(plan->s_up, plan->ev_comp[k], 0));
+  if (st == PAI_OK)
+    st = cuda_status(cudaMemcpyAsync(plan->d_pipe_in[k], h_p, plan->data_total * sizeof(float),
+                                     cudaMemcpyHostToDevice, plan->s_up));
+  if (st == PAI_OK) st = cuda_status(cudaEventRecord(plan->ev_up[k], plan->s_up));
+  if (st == PAI_OK) st = cuda_status(cudaStreamWaitEvent(plan->stream, plan->ev_up[k], 0));
+  if (st == PAI_OK && reuse) st = cuda_status(cudaStreamWaitEvent(plan->stream, plan->ev_down[k], 0));
+  if (st == PAI_OK) st = run(plan, plan->d_pipe_in[k], plan->d_pipe_out[k], false);
+  if (st == PAI_OK) st = cuda_status(cudaEventRecord(plan->ev_comp[k], plan->stream));
+  if (st == PAI_OK) st = cuda_status(cudaStreamWaitEvent(plan->s_down, plan->ev_comp[k], 0));
+  if (st == PAI_OK)
+    st = cuda_status(cudaMemcpyAsync(h_f, plan->d_pipe_out[k], plan->img_total * sizeof(float),
+                                     cudaMemcpyDeviceToHost, plan->s_down));
+  if (st == PAI_OK) st = cuda_status(cudaEventRecord(plan->ev_down[k], plan->s_down));
+  if (st == PAI_OK) ++plan->host_calls;
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_host_wait(pai_plan_t plan) {
+  if (!plan) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = PAI_OK;
+  if (plan->s_down) st = cuda_status(cudaStreamSynchronize(plan->s_down));
+  if (st == PAI_OK && plan->s_up) st = cuda_status(cudaStreamSynchronize(plan->s_up));
   if (st == PAI_OK) st = cuda_status(cudaStreamSynchronize(plan->stream));
   if (prev != plan->device) cudaSetDevice(prev);
   return st;

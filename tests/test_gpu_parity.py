@@ -120,12 +120,58 @@ def test_graph_cache_distinct_buffers(pai):
     assert rel(to_np(o2), _ref(g, ph.random_data(27, g))) < TOL
 
 
-def test_reconstruct_host_matches_device(pai):
+@pytest.mark.parametrize("pin_in,pin_out", [(True, True), (False, False), (True, False), (False, True)])
+def test_reconstruct_host_matches_device(pai, pin_in, pin_out, pipeline):
+    """Host buffers, page-locked or pageable, in any combination: the device
+    result bit for bit."""
     import torch
     prob = ph.plain_2d(4)
     plan = pai.Plan(gdict(prob.geom))
-    host = torch.from_numpy(prob.p.astype(np.float32)).pin_memory()
-    fh = plan.reconstruct_host(host)
+    host = torch.from_numpy(prob.p.astype(np.float32))
+    if pin_in:
+        host = host.pin_memory()
+    out = torch.full(plan._out_shape("nz"), float("nan"), dtype=torch.float32)
+    if pin_out:
+        out = out.pin_memory()
+    fh = plan.reconstruct_host(host, out)
+    fd = plan.reconstruct(host.cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(fh, fd.cpu())
+    # again with different data in the same buffers (the cached graph reads them afresh)
+    host.copy_(torch.from_numpy(ph.plain_2d(5).p.astype(np.float32)))
+    fh = plan.reconstruct_host(host, out)
+    fd = plan.reconstruct(host.cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(fh, fd.cpu())
+
+
+def test_reconstruct_host_async_pipeline(pai, pipeline):
+    """Pipelined host calls: five frames through alternating page-locked buffers,
+    each image equal to the device result of its own frame."""
+    import torch
+    prob = ph.plain_2d(6)
+    g = prob.geom
+    plan = pai.Plan(gdict(g))
+    frames = [ph.random_data(60 + i, g).astype(np.float32) for i in range(5)]
+    ins = [torch.from_numpy(f).pin_memory() for f in frames]
+    outs = [torch.full(plan._out_shape("nz"), float("nan"), dtype=torch.float32).pin_memory() for _ in frames]
+    for i in range(5):
+        plan.reconstruct_host_async(ins[i], outs[i])
+    plan.host_wait()
+    for i in range(5):
+        fd = plan.reconstruct(ins[i].cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(outs[i], fd.cpu()), i
+
+
+def test_reconstruct_host_batched_3d(pai):
+    import torch
+    geoms = [ph.Geometry(dim=3, nx=32, ny=32, nt=64, nz=32), ph.Geometry(dim=2, nx=100, nt=130, nz=64)]
+    plan = pai.Plan([gdict(g) for g in geoms])
+    host = torch.from_numpy(np.concatenate([ph.random_data(30 + i, g).ravel() for i, g in enumerate(geoms)])
+                            .astype(np.float32)).pin_memory()
+    out = torch.empty(plan.image_numel, dtype=torch.float32).pin_memory()
+    fh = plan.reconstruct_host(host, out)
     fd = plan.reconstruct(host.cuda())
     torch.cuda.synchronize()
     assert torch.equal(fh, fd.cpu())
