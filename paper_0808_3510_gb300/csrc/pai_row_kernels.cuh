@@ -783,11 +783,12 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     // list is sorted); for each tap t in turn the head of every run evaluates
     // the tap weight of each of its nodes (tap index uniform over the CTA, so
     // the polynomial coefficients stay constant-bank operands) and adds the
-    // run's sum to its cell.  Within a chunk distinct runs have distinct j0 and
-    // the chunk spans fewer than M - 2H cells, so in one tap phase no two heads
-    // write the same cell; a barrier separates the tap phases.  Every cell
-    // receives its terms in a fixed order (chunk, tap, node): deterministic, no
-    // atomics.
+    // run's sum to its cell.  Taps run in the order 0, 2H-1, 1, 2H-2, ... so a
+    // tap and its mirror share one evaluation of the pair polynomials.  Within
+    // a chunk distinct runs have distinct j0 and the chunk spans fewer than
+    // M - 2H cells, so in one tap phase no two heads write the same cell; a
+    // barrier separates the tap phases.  Every cell receives its terms in a
+    // fixed order (chunk, tap, node): deterministic, no atomics.
     {
       const int CH = L.chunk;  // <= tpr
       for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
@@ -806,34 +807,49 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
             while (lane + run < cn && __float_as_int(N[c0 + lane + run].x) == j0) ++run;
           }
         }
+        // the head's own node stays in registers for all taps; its polynomial
+        // pair (E_p, O_p) serves tap p and its mirror 2H-1-p, which run in
+        // consecutive phases
+        const float4 nd0 = run > 0 ? N[c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float z0 = nd0.y - 0.5f, z0sq = z0 * z0;
         __syncthreads();  // previous chunk's writes (or the zeroing) complete
 #pragma unroll
-        for (int t = 0; t < 2 * H; ++t) {
-          if (run > 0) {
-            // tap t of pair p: w(z) = E_p(z^2) +- z O_p(z^2), z = fr - 1/2 (sign + for t < H)
-            const int p = t < H ? t : 2 * H - 1 - t;
-            float sx = 0.f, sy = 0.f;
-            for (int r = 0; r < run; ++r) {
-              const float4 nd = N[c0 + lane + r];
-              const float z = t < H ? nd.y - 0.5f : 0.5f - nd.y;
-              const float z2 = z * z;
-              float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+        for (int p = 0; p < H; ++p) {
+          float E0 = W.ce[p][kHalfCoef - 1], O0 = W.co[p][kHalfCoef - 1];
 #pragma unroll
-              for (int e = kHalfCoef - 2; e >= 0; --e) {
-                E = fmaf(E, z2, W.ce[p][e]);
-                O = fmaf(O, z2, W.co[p][e]);
-              }
-              const float w = fmaf(z, O, E);
-              sx = fmaf(w, nd.z, sx);
-              sy = fmaf(w, nd.w, sy);
-            }
-            const int gi = PADI((j0 + t - H + 1) & mask);
-            float2 x = X[gi];
-            x.x += sx;
-            x.y += sy;
-            X[gi] = x;
+          for (int e = kHalfCoef - 2; e >= 0; --e) {
+            E0 = fmaf(E0, z0sq, W.ce[p][e]);
+            O0 = fmaf(O0, z0sq, W.co[p][e]);
           }
-          __syncthreads();
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            // tap t = p (side 0) or 2H-1-p (side 1): w(z) = E_p(z^2) +- z O_p(z^2), z = fr - 1/2
+            if (run > 0) {
+              const float w0 = side == 0 ? fmaf(z0, O0, E0) : fmaf(-z0, O0, E0);
+              float sx = w0 * nd0.z, sy = w0 * nd0.w;
+              for (int r = 1; r < run; ++r) {
+                const float4 nd = N[c0 + lane + r];
+                const float z = side == 0 ? nd.y - 0.5f : 0.5f - nd.y;
+                const float z2 = z * z;
+                float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+                for (int e = kHalfCoef - 2; e >= 0; --e) {
+                  E = fmaf(E, z2, W.ce[p][e]);
+                  O = fmaf(O, z2, W.co[p][e]);
+                }
+                const float w = fmaf(z, O, E);
+                sx = fmaf(w, nd.z, sx);
+                sy = fmaf(w, nd.w, sy);
+              }
+              const int t = side == 0 ? p : 2 * H - 1 - p;
+              const int gi = PADI((j0 + t - H + 1) & mask);
+              float2 x = X[gi];
+              x.x += sx;
+              x.y += sy;
+              X[gi] = x;
+            }
+            __syncthreads();
+          }
         }
       }
     }
