@@ -206,6 +206,39 @@ def test_batched_uneven_matches_oracle_and_single_plans(pai, pipeline):
     assert off == out.size
 
 
+def test_batched_64_full_size_sampled_rows(pai):
+    """The 64-problem batch at full size (nx = 2 U{128..1024}, nt = 2 U{256..2048},
+    nz = nt/2; the benchmark's batched workload and launch): for every problem,
+    three spectrum rows of the one batched launch against the oracle's row-by-row
+    direct sums, and the images of four problems against FP64 inverse FFTs of
+    the GPU's own spectra."""
+    geoms = ph.batched_2d_geometries(0, 64)
+    rng = np.random.default_rng(11)
+    datas = [rng.standard_normal(g.data_shape).astype(np.float32) for g in geoms]
+    plan = pai.Plan([gdict(g) for g in geoms])
+    flat = to_gpu(np.concatenate([d.ravel() for d in datas]))
+    S = plan.spectrum(flat).cpu().numpy()
+    f = to_np(plan.reconstruct(flat))
+    so = fo = 0
+    for i, (g, d) in enumerate(zip(geoms, datas)):
+        nzh = g.nz // 2
+        Si = S[so: so + g.nx * (nzh + 1)].reshape(g.nx, nzh + 1)
+        fi = f[fo: fo + g.nx * g.nz].reshape(g.nx, g.nz)
+        so += g.nx * (nzh + 1)
+        fo += g.nx * g.nz
+        ks = np.array([0, int(rng.integers(1, g.nx // 2)), -int(rng.integers(1, g.nx // 2))])
+        F = oracle.spectrum_rows(g, d.astype(np.float64), ks)
+        Fneg = oracle.spectrum_rows(g, d.astype(np.float64), -ks)
+        for r, k in enumerate(ks):
+            exp = F[r, : nzh + 1].copy() / (g.nx * g.nz)
+            exp[nzh] = 0.5 * (F[r, nzh] + np.conj(Fneg[r, nzh])) / (g.nx * g.nz)
+            assert rel(Si[k % g.nx], exp) < TOL, (i, k)
+        if i % 16 == 0:
+            ref = np.fft.irfft2(Si.astype(np.complex128) * (g.nx * g.nz), s=(g.nx, g.nz))
+            assert rel(fi, ref) < TOL, i
+    assert so == S.size and fo == f.size
+
+
 def test_large_2d_sampled_rows(pai, pipeline):
     """2-D large (2048 x 4096 -> 2048 x 2048, c = 2, K = 4) in the launch
     configuration the benchmark times: sampled spectrum rows against the
