@@ -229,6 +229,38 @@ pai_status pai_destroy(pai_plan_t plan);
 pai_status pai_window_probe(int H, double beta, double c, int n, const double* y, double* phi_out,
                             double* pred_err, double* fit_err);
 
+/* Discrete forward model: the detector data of an initial pressure (the
+ * operator Q of Sec. 2: the wave equation's solution on the detector plane,
+ * depth 0, at the recorded times), for iterative or regularised
+ * reconstruction around pai_reconstruct / pai_adjoint.
+ *
+ * Definition.  The image f[x][y][q] (the image grid of g) is zero-padded to a
+ * periodic box of bx x by x bz cells, each extent the next power of two >= the
+ * image extent + ceil(c nt dt / spacing) + 2 (so no periodic image of the
+ * object reaches the detectors within the recorded time); the data are the
+ * exact wave-equation solution for the trigonometric interpolant of the
+ * padded image, p(x, t_n) = Re (1/(bx by bz)) sum_K fhat_box(K) cos(c |K| t_n)
+ * e^{i K_lat x}, at the detector positions x < nx (y < ny).  Per lateral box
+ * frequency the sum over depth frequencies is a cosine sum at the
+ * nonuniform frequencies c|K|: a type-1 NUFFT (nodes +-nu, the Kaiser-Bessel
+ * window of the plan parameters), evaluated by the adjoint pipeline on the
+ * box.
+ *
+ * pai_forward_plan: g as for pai_plan (method KB or TSINC); box extents up to
+ * 16384 laterally and 8192 in depth (PAI_ERR_UNSUPPORTED beyond); allocates
+ * the box buffers (4 (bx by bz + bx by nt) bytes) besides the plan's own.
+ * The returned plan accepts pai_forward_model, pai_forward_box, pai_get_info
+ * (describing the box geometry), pai_set_stream, pai_launch_count,
+ * pai_profile_stages with adjoint = 1 (box-sized buffers) and pai_destroy;
+ * the other calls return PAI_ERR_INVALID_ARG.
+ * pai_forward_model: d_f device FP32 image [nx][ny][nz], read only; d_p
+ * device FP32 data [nx][ny][nt], overwritten.  Asynchronous on the plan's
+ * stream.                                                                    */
+pai_status pai_forward_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out);
+pai_status pai_forward_model(pai_plan_t plan, const float* d_f, float* d_p);
+/* Box extents of a forward-model plan (by = 1 in 2-D).                       */
+pai_status pai_forward_box(pai_plan_t plan, int* bx, int* by, int* bz);
+
 /* Size of the static device scratch array used by pai_spectrum_rows_noalloc. */
 #define PAI_NOALLOC_SCRATCH_BYTES (1u << 20)
 

@@ -98,6 +98,8 @@ def _load():
         lib.oracle_adjoint.restype = i
         lib.oracle_adjoint_box.argtypes = [G, dp, i, i, i, i, i, i, dp, i]
         lib.oracle_adjoint_box.restype = i
+        lib.oracle_forward_model.argtypes = [G, dp, i, i, i, dp, i]
+        lib.oracle_forward_model.restype = i
         lib.oracle_threads.argtypes = [i]
         lib.oracle_threads.restype = i
         _lib = lib
@@ -272,3 +274,37 @@ def adjoint_box(g, h: np.ndarray, x, y, n, nthreads: int = 0) -> np.ndarray:
     if rc:
         raise MemoryError("oracle_adjoint_box failed")
     return out.reshape((cx, cn)) if gg.dim == 2 else out
+
+
+def forward_box(g) -> tuple:
+    """Box extents of the discrete forward model: per axis the next power of two
+    (at least 32) >= the image extent + ceil(c nt dt / spacing) + 2."""
+    import math
+    gg = _geom(g)
+
+    def ext(n, d):
+        need = n + math.ceil(gg.c * gg.nt * gg.dt / d - 1e-9) + 2
+        b = 32
+        while b < need:
+            b *= 2
+        return b
+    return (ext(gg.nx, gg.dx), ext(gg.ny, gg.dy) if gg.dim == 3 else 1, ext(gg.nz, gg.dz))
+
+
+def forward_model(g, f: np.ndarray, box=None, nthreads: int = 0) -> np.ndarray:
+    """Discrete forward model (Sec. 2, the operator Q): detector data of the
+    initial pressure f on the image grid, the exact wave-equation solution for
+    the trigonometric interpolant of f zero-padded to the periodic box ``box``
+    (default :func:`forward_box`), by direct sums; returns [nx][(ny)][nt]."""
+    gg = _geom(g)
+    a = np.ascontiguousarray(f, dtype=np.float64)
+    if a.size != gg.nx * gg.ny * gg.nz:
+        raise ValueError("image size does not match the geometry")
+    bx, by, bz = box if box is not None else forward_box(g)
+    out = np.empty(_shape_data(gg), np.float64)
+    rc = _load().oracle_forward_model(ctypes.byref(gg), _dptr(a), bx, by, bz, _dptr(out), nthreads)
+    if rc == -2:
+        raise ValueError("box smaller than the image")
+    if rc:
+        raise MemoryError("oracle_forward_model failed")
+    return out.reshape(_out_shape(gg, gg.nt))

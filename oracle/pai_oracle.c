@@ -681,4 +681,133 @@ int oracle_adjoint_box(const oracle_geom* g, const double* h, int x0, int cx, in
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Discrete forward model (the operator Q of Sec. 2 on a padded box)    */
+/* ------------------------------------------------------------------ */
+/*
+ * The image f[x][y][q] sits at the origin of a periodic box of bx x by x bz
+ * cells (zeros elsewhere).  The wave equation with initial pressure equal to
+ * the box's trigonometric interpolant and zero initial velocity has the
+ * solution  sum_K fhat(K) cos(c |K| t) e^{i K.r} / (bx by bz);  at the
+ * detectors (depth 0, lateral cells x < nx, y < ny) and times t_n = n dt:
+ *   p[x][y][n] = Re (1/(bx by bz)) sum_{kx,ky,l} fhat[kx][ky][l]
+ *                cos(2 pi nu n / nt) e^{+2 pi i (kx x/bx + ky y/by)},
+ *   nu = c dt nt |K| / (2 pi),  K = 2 pi (kx/(bx dx), ky/(by dy), l/(bz dz)),
+ * signed frequencies, fhat the unnormalised DFT of the padded image.
+ */
+typedef struct {
+  const oracle_geom* g; int bx, by, bz;
+  const double* f; cplx* A; cplx* B; cplx* C; const cplx* wx; const cplx* wy; const cplx* wz;
+  double* out;
+} fm_ctx;
+
+/* A[kx][y][q] = sum_{x < nx} e^{-2 pi i kx x / bx} f[x][y][q] */
+static void fm_x(void* a, long kx) {
+  fm_ctx* c = (fm_ctx*)a;
+  const oracle_geom* g = c->g;
+  size_t plane = (size_t)g->ny * g->nz;
+  cplx* d = c->A + (size_t)kx * plane;
+  for (size_t i = 0; i < plane; ++i) d[i] = 0;
+  for (int x = 0; x < g->nx; ++x) {
+    cplx w = c->wx[((long)kx * x) % c->bx];
+    const double* s = c->f + (size_t)x * plane;
+    for (size_t i = 0; i < plane; ++i) d[i] += w * s[i];
+  }
+}
+
+/* B[kx][ky][q] = sum_{y < ny} e^{-2 pi i ky y / by} A[kx][y][q] */
+static void fm_y(void* a, long kx) {
+  fm_ctx* c = (fm_ctx*)a;
+  const oracle_geom* g = c->g;
+  const cplx* s = c->A + (size_t)kx * g->ny * g->nz;
+  cplx* d = c->B + (size_t)kx * c->by * g->nz;
+  for (int ky = 0; ky < c->by; ++ky) {
+    cplx* dd = d + (size_t)ky * g->nz;
+    for (int q = 0; q < g->nz; ++q) dd[q] = 0;
+    for (int y = 0; y < g->ny; ++y) {
+      cplx w = c->wy[((long)ky * y) % c->by];
+      const cplx* ss = s + (size_t)y * g->nz;
+      for (int q = 0; q < g->nz; ++q) dd[q] += w * ss[q];
+    }
+  }
+}
+
+/* C[kx][ky][n] = (1/(bx by bz)) sum_l cos(2 pi nu n/nt) sum_{q < nz} e^{-2 pi i l q/bz} B[kx][ky][q] */
+static void fm_t(void* a, long kx) {
+  fm_ctx* c = (fm_ctx*)a;
+  const oracle_geom* g = c->g;
+  int skx = signed_freq((int)kx, c->bx);
+  cplx* F = (cplx*)malloc(sizeof(cplx) * (size_t)c->bz);
+  double scale = 1.0 / ((double)c->bx * c->by * c->bz);
+  for (int ky = 0; ky < c->by; ++ky) {
+    int sky = signed_freq(ky, c->by);
+    const cplx* s = c->B + ((size_t)kx * c->by + ky) * g->nz;
+    for (int l = 0; l < c->bz; ++l) {
+      cplx acc = 0;
+      for (int q = 0; q < g->nz; ++q) acc += c->wz[((long)l * q) % c->bz] * s[q];
+      F[l] = acc;
+    }
+    cplx* d = c->C + ((size_t)kx * c->by + ky) * g->nt;
+    for (int n = 0; n < g->nt; ++n) d[n] = 0;
+    for (int l = 0; l < c->bz; ++l) {
+      int sl = signed_freq(l, c->bz);
+      double Kx = TWO_PI * skx / (c->bx * g->dx);
+      double Ky = (g->dim == 3) ? TWO_PI * sky / (c->by * g->dy) : 0.0;
+      double Kz = TWO_PI * sl / (c->bz * g->dz);
+      double nu = g->c * g->dt * g->nt * sqrt(Kx * Kx + Ky * Ky + Kz * Kz) / TWO_PI;
+      for (int n = 0; n < g->nt; ++n) {
+        double turns = nu * (double)n / (double)g->nt;
+        turns -= floor(turns);
+        d[n] += cos(TWO_PI * turns) * F[l];
+      }
+    }
+    for (int n = 0; n < g->nt; ++n) d[n] *= scale;
+  }
+  free(F);
+}
+
+/* out[x][y][n] = Re sum_{kx,ky} e^{+2 pi i (kx x/bx + ky y/by)} C[kx][ky][n], x < nx, y < ny */
+static void fm_lat(void* a, long x) {
+  fm_ctx* c = (fm_ctx*)a;
+  const oracle_geom* g = c->g;
+  cplx* acc = (cplx*)calloc((size_t)g->ny * g->nt, sizeof(cplx));
+  for (int kx = 0; kx < c->bx; ++kx) {
+    cplx wxv = conj(c->wx[((long)kx * x) % c->bx]);
+    for (int ky = 0; ky < c->by; ++ky) {
+      const cplx* s = c->C + ((size_t)kx * c->by + ky) * g->nt;
+      for (int y = 0; y < g->ny; ++y) {
+        cplx w = wxv * conj(c->wy[((long)ky * y) % c->by]);
+        cplx* d = acc + (size_t)y * g->nt;
+        for (int n = 0; n < g->nt; ++n) d[n] += w * s[n];
+      }
+    }
+  }
+  for (size_t i = 0; i < (size_t)g->ny * g->nt; ++i) c->out[(size_t)x * g->ny * g->nt + i] = creal(acc[i]);
+  free(acc);
+}
+
+int oracle_forward_model(const oracle_geom* g, const double* f, int bx, int by, int bz, double* p, int threads) {
+  if (bx < g->nx || bz < g->nz || (g->dim == 3 && by < g->ny) || bx < 1 || bz < 1) return -2;
+  if (g->dim != 3) by = 1;
+  fm_ctx c;
+  c.g = g; c.bx = bx; c.by = by; c.bz = bz; c.f = f; c.out = p;
+  c.A = (cplx*)malloc(sizeof(cplx) * (size_t)bx * g->ny * g->nz);
+  c.B = (cplx*)malloc(sizeof(cplx) * (size_t)bx * by * g->nz);
+  c.C = (cplx*)malloc(sizeof(cplx) * (size_t)bx * by * g->nt);
+  cplx* wx = twiddle_table(bx);
+  cplx* wy = twiddle_table(by);
+  cplx* wz = twiddle_table(bz);
+  c.wx = wx; c.wy = wy; c.wz = wz;
+  if (!c.A || !c.B || !c.C || !wx || !wy || !wz) {
+    free(c.A); free(c.B); free(c.C); free(wx); free(wy); free(wz);
+    return -1;
+  }
+  parallel_rows(fm_x, &c, bx, threads);
+  parallel_rows(fm_y, &c, bx, threads);
+  parallel_rows(fm_t, &c, bx, threads);
+  parallel_rows(fm_lat, &c, g->nx, threads);
+  free(c.A); free(c.B); free(c.C); free(wx); free(wy); free(wz);
+  return 0;
+}
+
 int oracle_threads(int requested) { return n_threads(requested); }

@@ -117,6 +117,13 @@ def load_library() -> ctypes.CDLL:
             getattr(lib, name).restype = st
         lib.pai_host_wait.argtypes = [vp]
         lib.pai_host_wait.restype = st
+        lib.pai_forward_plan.argtypes = [G, vp, ctypes.POINTER(vp)]
+        lib.pai_forward_plan.restype = st
+        lib.pai_forward_model.argtypes = [vp, fp, fp]
+        lib.pai_forward_model.restype = st
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.pai_forward_box.argtypes = [vp, ip, ip, ip]
+        lib.pai_forward_box.restype = st
         lib.pai_profile_stages.argtypes = [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.pai_profile_stages.restype = st
         lib.pai_set_stream.argtypes = [vp, vp]
@@ -347,6 +354,77 @@ class Plan:
         n = ctypes.c_longlong()
         _check(self._lib.pai_launch_count(self._h, ctypes.byref(n)), "pai_launch_count")
         return int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pai_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ForwardModel:
+    """Discrete forward model (``pai_forward_plan`` / ``pai_forward_model``): detector
+    data of an initial pressure on the image grid, the wave equation solved
+    exactly for its trigonometric interpolant in a zero-padded periodic box.
+    Calls run on torch's current stream."""
+
+    def __init__(self, g, stream: Optional[torch.cuda.Stream] = None):
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_0808_3510_gb300 needs a CUDA device")
+        self.geom = geometry(g)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = s.cuda_stream
+        h = ctypes.c_void_p()
+        _check(lib.pai_forward_plan(ctypes.byref(self.geom), ctypes.c_void_p(self._stream), ctypes.byref(h)),
+               "pai_forward_plan")
+        self._h = h
+        self._lib = lib
+        b = [ctypes.c_int() for _ in range(3)]
+        _check(lib.pai_forward_box(h, *[ctypes.byref(v) for v in b]), "pai_forward_box")
+        self.box = tuple(v.value for v in b)
+
+    def __call__(self, f: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        g = self.geom
+        n_img, n_dat = _numel(g, g.nz), _numel(g, g.nt)
+        if not isinstance(f, torch.Tensor) or f.device != self.device or f.dtype != torch.float32 \
+                or not f.is_contiguous() or f.numel() != n_img:
+            raise ValueError(f"f must be a contiguous float32 tensor on {self.device} with {n_img} elements")
+        if out is None:
+            out = torch.empty(_shape(g, g.nt), device=self.device, dtype=torch.float32)
+        if out.device != self.device or out.dtype != torch.float32 or not out.is_contiguous() \
+                or out.numel() != n_dat:
+            raise ValueError(f"out must be a contiguous float32 tensor on {self.device} with {n_dat} elements")
+        cur = torch.cuda.current_stream(self.device).cuda_stream
+        if cur != self._stream:
+            _check(self._lib.pai_set_stream(self._h, ctypes.c_void_p(cur)), "pai_set_stream")
+            self._stream = cur
+        _check(self._lib.pai_forward_model(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+               "pai_forward_model")
+        return out
+
+    @property
+    def info(self) -> dict:
+        i = PlanInfo()
+        _check(self._lib.pai_get_info(self._h, ctypes.byref(i)), "pai_get_info")
+        return i.as_dict()
+
+    def profile_stages(self, reps: int = 10):
+        """Mean device ms of (image-side transforms, forward-model row kernel, lateral inverse) on the box."""
+        bx, by, bz = self.box
+        g = self.geom
+        x = torch.zeros(bx * by * bz, device=self.device, dtype=torch.float32)
+        y = torch.empty(bx * by * g.nt, device=self.device, dtype=torch.float32)
+        ms = (ctypes.c_double * 3)()
+        _check(self._lib.pai_profile_stages(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                            int(reps), 1, ms), "pai_profile_stages")
+        return [ms[0], ms[1], ms[2]]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

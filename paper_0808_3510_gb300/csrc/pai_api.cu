@@ -101,6 +101,12 @@ struct pai_plan_s {
   cudaStream_t s_up = nullptr, s_down = nullptr;
   cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
   long long host_calls = 0;
+  // discrete forward model plans (pai_forward_plan): this plan's geometry is
+  // the padded box; the image / detector geometry and the box buffers
+  bool qmode = false;
+  pai_geometry qimg{};
+  float* d_qin = nullptr;   // box image
+  float* d_qout = nullptr;  // box data
   bool use_graph = true;
   std::vector<GraphEntry> graphs;
   long long own_kernels = 0, fft_execs = 0;
@@ -204,6 +210,8 @@ void release(pai_plan_s* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   if (P->s_up) cudaStreamSynchronize(P->s_up);
   if (P->s_down) cudaStreamSynchronize(P->s_down);
+  cudaFree(P->d_qin);
+  cudaFree(P->d_qout);
   for (int k = 0; k < 2; ++k) {
     cudaFree(P->d_pipe_in[k]);
     cudaFree(P->d_pipe_out[k]);
@@ -435,7 +443,7 @@ pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
 }
 
 // Plan construction shared by pai_plan and pai_plan_batched.
-pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_s** out) {
+pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_s** out, bool qmode = false) {
   if (!gs || !out || count < 1) return PAI_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) PAI_TRY(validate(gs[i]));
   for (int i = 1; i < count; ++i)
@@ -538,8 +546,26 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       }
       zf = zf && nz_ok && lat_ok;
     }
+    if (qmode) {
+      // the forward model runs on the depth-row adjoint pipeline only
+      zf = true;
+      for (auto& p : P->probs) {
+        const pai_geometry& g = p.g;
+        const bool nz_ok = (g.nz & (g.nz - 1)) == 0 && g.nz >= 32 && g.nz <= 16384;
+        bool lat_ok;
+        if (g.dim == 2) {
+          lat_ok = lateral_supported(g.nx, g.nt) && lateral_supported(g.nx, g.nz);
+        } else {
+          const int h = g.ny / 2 + 1;
+          lat_ok = lateral_supported(g.ny, g.nt) && lateral_supported(g.ny, g.nz) &&
+                   lateral_supported(g.nx, h * g.nt) && lateral_supported(g.nx, h * g.nz);
+        }
+        if (!(nz_ok && lat_ok)) return PAI_ERR_UNSUPPORTED;
+      }
+    }
     P->zf = zf;
     P->zf_adj = zf;
+    P->qmode = qmode;
   }
 
   // ---- layout -------------------------------------------------------------
@@ -612,6 +638,10 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     r.rowS = reinterpret_cast<const float2*>(P->d_tables + p.rowS_off);
     r.zt = reinterpret_cast<const float4*>(P->d_tables + p.zt_off);
     fill_row_scalars(p.g, p.M, r);
+    if (qmode) {
+      r.qmode = 1;
+      r.wscale = (float)(0.5 / ((double)r.n1 * r.n2 * p.g.nz));
+    }
   }
 
   // ---- cuFFT ----------------------------------------------------------------
@@ -720,7 +750,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   };
   // ---- tuner: pick the CTA size by timing the forward row kernel -------------
   const char* env_tune = std::getenv("PAI_AUTOTUNE");
-  bool tune = !(env_tune && env_tune[0] == '0') && !env_t;
+  bool tune = !(env_tune && env_tune[0] == '0') && !env_t && !qmode;
   if (tune) {
     int best_T = 0;
     float best_ms = 1e30f;
@@ -833,6 +863,31 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   return PAI_OK;
 }
 
+// Zero-padded copy of an image [nx][ny][nz] into the box [bx][by][bz]
+// (the image at the box origin, zeros elsewhere); z fastest, coalesced.
+__global__ void pad_box_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
+                               int by, int bz, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(i % bz);
+    const long long xy = i / bz;
+    const int y = (int)(xy % by);
+    const int x = (int)(xy / by);
+    out[i] = (x < nx && y < ny && z < nz) ? in[((size_t)x * ny + y) * nz + z] : 0.0f;
+  }
+}
+
+// Box of the discrete forward model along one axis: room for the image and for
+// the distance sound travels in the recorded time, so that no periodic image of
+// the object reaches the detectors within it (next power of two).
+int forward_box_extent(int n, double d, const pai_geometry& g) {
+  const double travel = g.c * g.nt * g.dt / d;
+  const long long need = (long long)n + (long long)std::ceil(travel - 1e-9) + 2;
+  long long b = 32;
+  while (b < need) b <<= 1;
+  return b > (1 << 30) ? (1 << 30) : (int)b;
+}
+
 }  // namespace
 
 extern "C" {
@@ -849,17 +904,20 @@ pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream,
 
 pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f) {
   if (!plan || !d_p || !d_f) return PAI_ERR_INVALID_ARG;
+  if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   return run(plan, d_p, d_f, false);
 }
 
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar) {
   if (!plan || !d_h || !d_pbar) return PAI_ERR_INVALID_ARG;
+  if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   if (method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
   return run(plan, d_h, d_pbar, true);
 }
 
 pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat) {
   if (!plan || !d_p || !d_fhat) return PAI_ERR_INVALID_ARG;
+  if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
@@ -885,6 +943,7 @@ pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat) {
 
 pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
   if (!plan || !h_p || !h_f) return PAI_ERR_INVALID_ARG;
+  if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
@@ -912,6 +971,7 @@ pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
 // transforms, copy out, record ev_down.
 pai_status pai_reconstruct_host_async(pai_plan_t plan, const float* h_p, float* h_f) {
   if (!plan || !h_p || !h_f) return PAI_ERR_INVALID_ARG;
+  if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
@@ -964,6 +1024,7 @@ pai_status pai_host_wait(pai_plan_t plan) {
 pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, int reps, int adjoint, double* ms) {
   if (!plan || !d_in || !d_out || !ms || reps < 1) return PAI_ERR_INVALID_ARG;
   if (adjoint && method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
+  if (plan->qmode && !adjoint) return PAI_ERR_INVALID_ARG;  // a forward-model plan runs its adjoint pipeline
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
@@ -1052,6 +1113,71 @@ pai_status pai_window_probe(int H, double beta, double c, int n, const double* y
     *fit_err = fit_window(0, H, beta, &w);
   }
   return PAI_OK;
+}
+
+pai_status pai_forward_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out) {
+  if (!g || !out) return PAI_ERR_INVALID_ARG;
+  pai_geometry gi = *g;
+  if (gi.dim == 2) {
+    gi.ny = 1;
+    gi.dy = 1.0;
+  }
+  PAI_TRY(validate(gi));
+  if (gi.method != PAI_METHOD_KB && gi.method != PAI_METHOD_TSINC) return PAI_ERR_UNSUPPORTED;
+  pai_geometry gb = gi;
+  gb.nx = forward_box_extent(gi.nx, gi.dx, gi);
+  if (gi.dim == 3) gb.ny = forward_box_extent(gi.ny, gi.dy, gi);
+  gb.nz = forward_box_extent(gi.nz, gi.dz, gi);
+  if (gb.nx > 16384 || gb.ny > 16384 || gb.nz > 8192) return PAI_ERR_UNSUPPORTED;
+  pai_plan_s* P = nullptr;
+  PAI_TRY(build_plan(&gb, 1, cuda_stream, &P, true));
+  P->qimg = gi;
+  const size_t box_img = (size_t)gb.nx * gb.ny * gb.nz, box_dat = (size_t)gb.nx * gb.ny * gb.nt;
+  pai_status st = cuda_status(cudaMalloc(&P->d_qin, box_img * sizeof(float)));
+  if (st == PAI_OK) st = cuda_status(cudaMalloc(&P->d_qout, box_dat * sizeof(float)));
+  if (st != PAI_OK) {
+    release(P);
+    return st == PAI_ERR_CUDA ? PAI_ERR_OOM : st;
+  }
+  *out = P;
+  return PAI_OK;
+}
+
+pai_status pai_forward_box(pai_plan_t plan, int* bx, int* by, int* bz) {
+  if (!plan || !plan->qmode || !bx || !by || !bz) return PAI_ERR_INVALID_ARG;
+  const pai_geometry& g = plan->probs[0].g;
+  *bx = g.nx;
+  *by = g.dim == 3 ? g.ny : 1;
+  *bz = g.nz;
+  return PAI_OK;
+}
+
+pai_status pai_forward_model(pai_plan_t plan, const float* d_f, float* d_p) {
+  if (!plan || !d_f || !d_p) return PAI_ERR_INVALID_ARG;
+  if (!plan->qmode) return PAI_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  const pai_geometry& gi = plan->qimg;
+  const pai_geometry& gb = plan->probs[0].g;
+  const int by = gb.dim == 3 ? gb.ny : 1, ny = gi.dim == 3 ? gi.ny : 1;
+  const long long total = (long long)gb.nx * by * gb.nz;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+  const long long want = (total + 255) / 256;
+  const int blocks = (int)std::min<long long>(want, (long long)std::max(sms, 1) * 16);
+  pad_box_kernel<<<blocks, 256, 0, plan->stream>>>(d_f, plan->d_qin, gi.nx, ny, gi.nz, by, gb.nz, total);
+  pai_status st = cuda_status(cudaGetLastError());
+  if (st == PAI_OK) st = run(plan, plan->d_qin, plan->d_qout, true);
+  if (st == PAI_OK) {
+    // detectors x < nx (and y < ny) of the box data [bx][by][nt]
+    const size_t row = (size_t)ny * gi.nt * sizeof(float), pitch = (size_t)by * gi.nt * sizeof(float);
+    st = cuda_status(cudaMemcpy2DAsync(d_p, row, plan->d_qout, pitch, row, gi.nx, cudaMemcpyDeviceToDevice,
+                                       plan->stream));
+  }
+  if (st == PAI_OK) plan->own_kernels += 1;  // the pad kernel (the rest is counted by run)
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
 }
 
 const char* pai_status_string(pai_status s) {

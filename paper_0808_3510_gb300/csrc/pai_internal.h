@@ -51,6 +51,7 @@ struct RowProblem {
   int mshift;              // log2(M)
   int nzshift;             // log2(nz) when nz is a power of two, else 0
   int method;              // PAI_METHOD_*
+  int qmode;               // adjoint kernel evaluates the discrete forward model (depth-row layout only)
 };
 
 struct WorkItem {

@@ -351,7 +351,7 @@ __device__ __forceinline__ void node_position(float2 S, float4 zt, float B2hi, f
   float q = __fmul_rn(x0, x0);
   float qe = fmaf(x0, x0, -q);
   float r = __fadd_rn(__fsub_rn(__fsub_rn(y_hi, q), qe), y_lo);
-  float delta = r * (0.5f / x0);
+  float delta = x0 > 0.0f ? r * (0.5f / x0) : 0.0f;  // x = 0 only for the zero-frequency node
   float fl = floorf(x0);
   j0 = (int)fl;
   fr = __fadd_rn(__fsub_rn(x0, fl), delta);
@@ -697,7 +697,37 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     int nneg = 1, nn = 0;
     // ZF: the row's depth spectrum Fbar[l mod nz] (depth FFT of the lateral R2C of the image)
     const float2* Zs = P.fh + (size_t)(valid ? row : 0) * P.nz;
-    if (valid && ZF) {
+    if (valid && ZF && P.qmode) {
+      // Discrete forward model (the operator Q of Sec. 2 on a padded periodic
+      // box): the row's temporal samples are sum_j c_j cos(2 pi nu_j n / nt)
+      // over the depth frequencies j = 0..nz/2, nu_j >= 0 the frequency of
+      // |K| (j = 0 included: its frequency is the lateral |K|), with
+      // c_j = F[j] + F[-j] (F[0], F[nz/2] alone).  Each cosine is the node pair
+      // +-nu_j with value c_j / 2 (wscale holds 1 / (2 n_lat nz)); the spread
+      // below and the inverse FFT then sum the pairs like any adjoint row.
+      rg.S = P.rowS[row];
+      rg.mirror = true;
+      nneg = nzh + 1;
+      nn = 2 * nneg;
+      for (int j = lane; j <= nzh; j += tpr) {
+        const float4 zt = __ldg(&P.zt[j]);
+        int j0p, j0;
+        float frp, fr, x0;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+        negate_node(j0p, frp, j0, fr);
+        float2 y = Zs[j];
+        if (j > 0 && j < nzh) {
+          const float2 y2 = Zs[P.nz - j];
+          y.x += y2.x;
+          y.y += y2.y;
+        }
+        const float2 pb = make_float2(P.wscale * y.x, P.wscale * y.y);
+        const float2 qp = cmul(pb, node_phase(j0p, frp, nt, M, P.nt_over_M));
+        const float2 qn = cmul(pb, node_phase(j0, fr, nt, M, P.nt_over_M));
+        N[nneg + j] = make_float4(__int_as_float(j0p), frp, qp.x, qp.y);
+        N[nneg - 1 - j] = make_float4(__int_as_float(j0), fr, qn.x, qn.y);
+      }
+    } else if (valid && ZF) {
       rg.S = P.rowS[row];
       rg.mirror = true;
       nneg = nzh;
@@ -792,7 +822,8 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     {
       const int CH = L.chunk;  // <= tpr
       for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
-      const int half_chunks = ((P.nz >> 1) + CH - 1) / CH;  // uniform over the CTA's slots
+      const int list_max = (P.nz >> 1) + (P.qmode ? 1 : 0);  // nodes per sign list, at most
+      const int half_chunks = (list_max + CH - 1) / CH;         // uniform over the CTA's slots
       for (int c = 0; c < 2 * half_chunks; ++c) {
         const bool pos = c >= half_chunks;
         const int first = pos ? nneg : 0;
