@@ -415,6 +415,12 @@ class ForwardModel:
         _check(self._lib.pai_get_info(self._h, ctypes.byref(i)), "pai_get_info")
         return i.as_dict()
 
+    @property
+    def kernel_launches(self) -> int:
+        n = ctypes.c_longlong()
+        _check(self._lib.pai_launch_count(self._h, ctypes.byref(n)), "pai_launch_count")
+        return n.value
+
     def profile_stages(self, reps: int = 10):
         """Mean device ms of (image-side transforms, forward-model row kernel, lateral inverse) on the box."""
         bx, by, bz = self.box
