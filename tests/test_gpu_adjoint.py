@@ -21,6 +21,7 @@ CASES = [
     ph.Geometry(dim=3, nx=32, ny=32, nt=64, nz=32),
     ph.Geometry(dim=3, nx=64, ny=32, nt=128, nz=64, dy=1.2),
     ph.Geometry(dim=2, nx=256, nt=512, nz=256, dz=0.8),
+    ph.Geometry(dim=2, nx=8, nt=8192, nz=64, dt=0.25),  # the largest padded length, M = 16384
 ]
 
 

@@ -239,6 +239,23 @@ def test_batched_64_full_size_sampled_rows(pai):
     assert so == S.size and fo == f.size
 
 
+@pytest.mark.parametrize("method", ["kb", "tsinc", "linear"])
+def test_largest_padded_length(pai, method):
+    """nt = 8192 at c = 2: M = 16384, the largest padded length (1024 threads per row)."""
+    g = ph.Geometry(dim=2, nx=8, nt=8192, nz=64, dt=0.25)
+    p = ph.random_data(95, g)
+    plan = pai.Plan(gdict(g, oversampling=2, K=3, method=method))
+    assert plan.info["M"] == 16384 and plan.info["threads_per_cta"] == 1024
+    f = to_np(plan.reconstruct(to_gpu(p)))
+    p64 = np.asarray(p, dtype=np.float32).astype(np.float64)
+    if method == "kb":
+        ref = oracle.reconstruct(g, p64)
+    else:
+        import oracle.methods as om
+        ref = om.reconstruct(g, p64, method, 2.0, 3.0)
+    assert rel(f, ref) < TOL
+
+
 def test_large_2d_sampled_rows(pai, pipeline):
     """2-D large (2048 x 4096 -> 2048 x 2048, c = 2, K = 4) in the launch
     configuration the benchmark times: sampled spectrum rows against the
