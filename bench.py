@@ -37,13 +37,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "reconstructed voxels/s and NUFFT-kernel HBM GB/s at rel L2<=1e-5, batched vs plain"
+# workloads of several problems in one batched plan
+MULTI_CONFIGS = ("batched2d", "frames2d")
 # the GPU tests that hold each workload to the oracle
 PARITY_TESTS = {
     "large2d": "tests/test_gpu_parity.py::test_large_2d_sampled_rows",
     "plain2d": "tests/test_gpu_parity.py::test_plain_2d_128x256",
     "planar3d": "tests/test_gpu_parity.py::test_3d_planar_128",
     "adjoint3d": "tests/test_gpu_adjoint.py",
-    "batched2d": "tests/test_gpu_parity.py::test_batched_uneven_matches_oracle_and_single_plans",
+    "batched2d": "tests/test_gpu_parity.py::test_batched_64_full_size_sampled_rows",
+    "frames2d": "tests/test_gpu_parity.py::test_large_2d_sampled_rows (per frame), test_batched_*",
 }
 UNIT = "voxels/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -80,6 +83,11 @@ def workload(name: str, seed: int = 0):
         pr = ph.adjoint_3d(seed)
         return ("3-D planar detector: 256 x 256 detectors x 512 samples -> 256^3, uniform balls; oversampling 2, K = 3",
                 [gd(pr.geom, oversampling=2.0, K=3.0)], [pr.p.astype(np.float32)])
+    if name == "frames2d":
+        probs = [ph.large_2d(seed * 8 + i) for i in range(8)]
+        return ("8 frames of the 2-D large workload (2048 x 4096 -> 2048 x 2048, independent seeds) in one batched "
+                "plan; oversampling 2, K = 4", [gd(p.geom, oversampling=2.0, K=4.0) for p in probs],
+                [p.p.astype(np.float32) for p in probs])
     if name == "batched2d":
         probs = ph.batched_2d(seed)
         return ("64 uneven 2-D problems (nx = 2 U{128..1024}, nt = 2 U{256..2048}, nz = nt/2) in one plan; "
@@ -382,7 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="large2d", choices=["large2d", "plain2d", "planar3d", "adjoint3d",
-                                                            "batched2d", "forward3d", "forward2d"])
+                                                            "batched2d", "frames2d", "forward3d", "forward2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -436,11 +444,12 @@ def main():
     flat = np.concatenate([d.ravel() for d in datas]).astype(np.float32)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    plan = pai.Plan(geoms if args.config == "batched2d" else geoms[0])
+    multi = args.config in MULTI_CONFIGS
+    plan = pai.Plan(geoms if multi else geoms[0])
     p_host = torch.from_numpy(flat).pin_memory()
     p = p_host.to(dev)
     out = torch.empty(plan.image_numel, device=dev, dtype=torch.float32)
-    if args.config != "batched2d":
+    if not multi:
         out = out.view(plan._out_shape("nz"))
         p = p.view(plan._out_shape("nt"))
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
@@ -523,7 +532,7 @@ def main():
 
     # batched vs plain: the same problems as separate plans, one after another, no graph
     batched = None
-    if args.config == "batched2d":
+    if multi:
         os.environ["PAI_USE_GRAPH"] = "0"
         plans = [pai.Plan(g) for g in geoms]
         del os.environ["PAI_USE_GRAPH"]
@@ -555,6 +564,26 @@ def main():
                    "speedup": plain_ms / ms}
         for pl in plans:
             pl.close()
+        if args.config == "frames2d":
+            # the same frames through one graph-replayed single-frame plan each
+            plans = [pai.Plan(g) for g in geoms]
+            for _ in range(3):
+                for pl, a, o in zip(plans, ins, outs):
+                    pl.reconstruct(a, o)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for i in range(reps):
+                flush.fill_(float(i & 7))
+                e0.record(stream)
+                for pl, a, o in zip(plans, ins, outs):
+                    pl.reconstruct(a, o)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            batched["plain_graph_ms_per_step"] = tot / reps
+            batched["speedup_vs_plain_graph"] = (tot / reps) / ms
+            for pl in plans:
+                pl.close()
 
     # end to end through host memory: a stream of steps through the pipelined
     # host call (upload, transforms and download of consecutive steps overlap);
@@ -565,7 +594,7 @@ def main():
                "note": "the gradient step has no host-memory entry point; the forward's end-to-end "
                        "number is reported by --config planar3d / large2d"}
     elif not args.no_e2e:
-        src = p_host if args.config == "batched2d" else p_host.view(plan._out_shape("nt"))
+        src = p_host if multi else p_host.view(plan._out_shape("nt"))
         ins = [src, src.clone().pin_memory()]
         outs = [torch.empty(plan._out_shape("nz"), dtype=torch.float32).pin_memory() for _ in range(2)]
         for i in range(4):
