@@ -648,7 +648,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   size_t work = 0;
   for (auto& p : P->probs) PAI_TRY(make_cufft_plans(p, work));
   P->cufft_work = work;
-  P->nbranch = std::min(count, 8);
+  P->nbranch = std::min(count, 4);  // measured on the 64-problem batch: 4 beat 2, 6, 8, 16, 32
   if (P->nbranch > 1) {
     P->branch.resize(P->nbranch, nullptr);
     P->branch_work.resize(P->nbranch, nullptr);
