@@ -60,6 +60,7 @@ struct pai_plan_s {
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   std::vector<ProblemHost> probs;
   int H = 0, Mmax = 0, threads = 512, ctas = 0, ctas_adj = 0, fft_region = 0;
+  int threads_adj = 512, fft_region_adj = 0;  // the adjoint row kernel's own CTA shape
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
   int chunk = 128, bin_offset = 0, bin_slot = 0;  // adjoint sorted-bin spread
   int method = PAI_METHOD_KB;                       // PAI_METHOD_*, shared by the batch
@@ -265,7 +266,7 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.tw = P->d_tw;
   L.Mmax = P->TW;
   L.H = P->H;
-  L.fft_region = P->fft_region;
+  L.fft_region = adjoint ? P->fft_region_adj : P->fft_region;
   L.chunk = P->chunk;
   L.bin_offset = P->bin_offset;
   L.bin_slot = P->bin_slot;
@@ -387,7 +388,7 @@ pai_status enqueue_forward(pai_plan_s* P, const float* d_p, float* d_f, cudaStre
 
 pai_status enqueue_adjoint(pai_plan_s* P, const float* d_h, float* d_pbar, cudaStream_t s) {
   PAI_TRY(enqueue_first(P, d_h, s, true));
-  PAI_TRY(enqueue_row(P, true, s, P->threads, P->ctas_adj, P->smem_adj, P->zf_adj));
+  PAI_TRY(enqueue_row(P, true, s, P->threads_adj, P->ctas_adj, P->smem_adj, P->zf_adj));
   return enqueue_last(P, d_pbar, s, true);
 }
 
@@ -524,6 +525,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   const int tpr_max = P->Mmax / kElemsPerThread;
   const char* env_t = std::getenv("PAI_THREADS");
   int threads = env_t ? std::atoi(env_t) : 512;
+  // forward-model plans (no tuner): the spread's barriers favour small CTAs
+  if (qmode && !env_t) threads = 128;
   threads = std::max(threads, tpr_max);
   threads = std::max(threads, 64);
   // row slots of a CTA must tile it exactly: the CTA size is a power of two
@@ -701,21 +704,40 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
                                                  const std::pair<double, WorkItem>& b) { return a.first > b.first; });
     for (auto& t : tmp) items.push_back(t.second);
   };
+  // CTA shape of the forward row kernel: rows per CTA, shared memory, work items
   auto finish_shape = [&](int T) -> pai_status {
     for (int i = 0; i < count; ++i) rp[i].rpc = T / P->probs[i].tpr;
-    int node_cap = 0;
-    for (int i = 0; i < count; ++i) node_cap = std::max(node_cap, rp[i].rpc * (P->probs[i].g.nz + 2));
     P->threads = T;
     size_t region = 0;
     for (int i = 0; i < count; ++i)
       region = std::max(region, (size_t)rp[i].rpc * (size_t)rp[i].slot * sizeof(float2));
     P->fft_region = (int)(region / sizeof(float2));
     P->smem_fwd = region;
-    int nz_max = 0, rpc_max = 0;
+    if (P->smem_fwd > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
+    const int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H, P->zf);
+    if (occ_f < 1) return PAI_ERR_UNSUPPORTED;
+    std::vector<WorkItem> items;
+    build_items(T, items);
+    P->nitems_fwd = (int)items.size();
+    P->ctas = std::min(P->nitems_fwd, occ_f * sms);
+    cudaFree(P->d_items_fwd);
+    P->d_items_fwd = nullptr;
+    PAI_CUDA(cudaMalloc(&P->d_items_fwd, items.size() * sizeof(WorkItem)));
+    PAI_CUDA(cudaMemcpy(P->d_items_fwd, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    PAI_CUDA(cudaMemcpy(P->d_problems, rp.data(), count * sizeof(RowProblem), cudaMemcpyHostToDevice));
+    return PAI_OK;
+  };
+  // CTA shape of the adjoint row kernel (row slots, then the node lists)
+  auto finish_shape_adj = [&](int T) -> pai_status {
+    int node_cap = 0;
+    size_t region = 0;
     for (int i = 0; i < count; ++i) {
-      nz_max = std::max(nz_max, P->probs[i].g.nz);
-      rpc_max = std::max(rpc_max, rp[i].rpc);
+      const int rpc = T / P->probs[i].tpr;
+      node_cap = std::max(node_cap, rpc * (P->probs[i].g.nz + 2));
+      region = std::max(region, (size_t)rpc * (size_t)rp[i].slot * sizeof(float2));
     }
+    P->threads_adj = T;
+    P->fft_region_adj = (int)(region / sizeof(float2));
     // Chunk of the adjoint spread: at most the threads of a row slot (one node
     // per thread) and spanning fewer than M - 2H cells (same-sign nodes are at
     // most M c dt / (nz dz) cells apart).
@@ -731,21 +753,18 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->bin_slot = 0;
     P->bin_offset = (int)(region + (size_t)node_cap * sizeof(float4));
     P->smem_adj = (size_t)P->bin_offset;
-    if (P->smem_fwd > (size_t)smem_optin || P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
-    int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H, P->zf);
-    int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);
-    if (occ_f < 1 || occ_a < 1) return PAI_ERR_UNSUPPORTED;
+    if (P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
+    const int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);
+    if (occ_a < 1) return PAI_ERR_UNSUPPORTED;
     std::vector<WorkItem> items;
     build_items(T, items);
-    P->nitems_fwd = P->nitems_adj = (int)items.size();
-    P->ctas = std::min(P->nitems_fwd, occ_f * sms);
+    P->nitems_adj = (int)items.size();
     P->ctas_adj = std::min(P->nitems_adj, occ_a * sms);
-    cudaFree(P->d_items_fwd);
-    P->d_items_fwd = nullptr;
-    PAI_CUDA(cudaMalloc(&P->d_items_fwd, items.size() * sizeof(WorkItem)));
-    PAI_CUDA(cudaMemcpy(P->d_items_fwd, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
-    P->d_items_adj = P->d_items_fwd;
-    PAI_CUDA(cudaMemcpy(P->d_problems, rp.data(), count * sizeof(RowProblem), cudaMemcpyHostToDevice));
+    if (P->d_items_adj == P->d_items_fwd) P->d_items_adj = nullptr;
+    cudaFree(P->d_items_adj);
+    P->d_items_adj = nullptr;
+    PAI_CUDA(cudaMalloc(&P->d_items_adj, items.size() * sizeof(WorkItem)));
+    PAI_CUDA(cudaMemcpy(P->d_items_adj, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
     return PAI_OK;
   };
   // ---- tuner: pick the CTA size by timing the forward row kernel -------------
@@ -758,8 +777,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_pt, 0, pt_off * sizeof(float2)));
-    for (int T : {256, 512, 1024}) {
-      if (T < tpr_max || T < 64) continue;
+    for (int T : {64, 128, 256, 512, 1024}) {
+      if (T < tpr_max) continue;
       if (finish_shape(T) != PAI_OK) continue;
       float best = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
@@ -782,6 +801,41 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     // prefer the requested size; fall back to smaller CTAs if shared memory does not fit
     pai_status st = PAI_ERR_UNSUPPORTED;
     for (int T = threads; T >= std::max(tpr_max, 32) && st != PAI_OK; T /= 2) st = finish_shape(T);
+    if (st != PAI_OK) return st;
+  }
+  // ---- tuner: the adjoint row kernel's CTA size, timed the same way ----------
+  // (the spread's barriers and the forward's FFT passes favour different sizes)
+  int threads_adj = threads;
+  if (tune && !method_interp(P->method)) {
+    int best_T = 0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    PAI_CUDA(cudaEventCreate(&e0));
+    PAI_CUDA(cudaEventCreate(&e1));
+    PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
+    for (int T : {64, 128, 256, 512, 1024}) {
+      if (T < tpr_max) continue;
+      if (finish_shape_adj(T) != PAI_OK) continue;
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, P->cap_stream);
+        if (enqueue_row(P, true, P->cap_stream, T, P->ctas_adj, P->smem_adj, P->zf_adj) != PAI_OK) break;
+        cudaEventRecord(e1, P->cap_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+      }
+      if (best < best_ms) { best_ms = best; best_T = T; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (best_T) threads_adj = best_T;
+  }
+  {
+    pai_status st = PAI_ERR_UNSUPPORTED;
+    for (int T = threads_adj; T >= std::max(tpr_max, 32) && st != PAI_OK; T /= 2) st = finish_shape_adj(T);
     if (st != PAI_OK) return st;
   }
   // ---- tuner: when both pipelines apply, keep the faster one ----------------
@@ -1039,7 +1093,8 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
     if (st == PAI_OK) st = enqueue_first(plan, d_in, s, adjoint != 0);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[1], s));
     if (st == PAI_OK)
-      st = enqueue_row(plan, adjoint != 0, s, plan->threads, adjoint ? plan->ctas_adj : plan->ctas,
+      st = enqueue_row(plan, adjoint != 0, s, adjoint ? plan->threads_adj : plan->threads,
+                       adjoint ? plan->ctas_adj : plan->ctas,
                        adjoint ? plan->smem_adj : plan->smem_fwd, adjoint ? plan->zf_adj : plan->zf);
     if (st == PAI_OK) st = cuda_status(cudaEventRecord(ev[2], s));
     if (st == PAI_OK) st = enqueue_last(plan, d_out, s, adjoint != 0);
