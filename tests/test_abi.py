@@ -120,3 +120,21 @@ def test_window_probe_rejects_lemma_violations(pai):
     assert lib.pai_window_probe(6, 2.0 * math.pi, 2.0, 0, None, None, None, None) == 1   # alpha > pi(2c-1)
     assert lib.pai_window_probe(1, 1.5 * math.pi, 2.0, 0, None, None, None, None) == 1
     assert lib.pai_window_probe(6, 1.5 * math.pi, 1.0, 0, None, None, None, None) == 1
+
+
+def test_forward_plan_host_validation(pai):
+    """The forward-model plan validates its geometry and box on the host."""
+    lib = pai.load_library()
+    h = ctypes.c_void_p()
+    g = pai.geometry(dict(dim=2, nx=16, nt=32, nz=16))
+    g.nx = 7
+    assert lib.pai_forward_plan(ctypes.byref(g), None, ctypes.byref(h)) == 1
+    # a box beyond 8192 cells in depth: nz + c nt dt / dz + 2 > 8192
+    g = pai.geometry(dict(dim=2, nx=16, nt=8192, nz=16, dz=0.5))
+    assert lib.pai_forward_plan(ctypes.byref(g), None, ctypes.byref(h)) == 2
+    g = pai.geometry(dict(dim=2, nx=16, nt=32, nz=16, method="nearest"))
+    assert lib.pai_forward_plan(ctypes.byref(g), None, ctypes.byref(h)) == 2
+    assert not h.value
+    assert lib.pai_forward_model(None, None, None) == 1
+    bx = ctypes.c_int()
+    assert lib.pai_forward_box(None, ctypes.byref(bx), ctypes.byref(bx), ctypes.byref(bx)) == 1
