@@ -88,8 +88,7 @@ typedef struct {
                              oversampled DFT at omega = j/c (no window),
                              interpolated linearly / to the nearest node;
                              oversampling may be 1 (no oversampling).
-                           pai_adjoint supports KB and TSINC only.  All problems
-                           of a batch use the same method.                   */
+                           All problems of a batch use the same method.      */
 } pai_geometry;
 
 #define PAI_METHOD_KB 0
@@ -154,10 +153,9 @@ pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f);
  * forward image FFT, window spread from the nodes onto the oversampled grid
  * in gather form, inverse oversampled FFT, prescale, inverse lateral FFT).
  * d_h: device, FP32, image-shaped, read only.  d_pbar: device, FP32,
- * data-shaped, overwritten.  Asynchronous on the plan's stream.
- * PAI_ERR_UNSUPPORTED for plans of the interpolation methods (linear,
- * nearest): the transposed spread exists for the windowed methods (KB,
- * truncated sinc) only.                                                      */
+ * data-shaped, overwritten.  Asynchronous on the plan's stream.  For the
+ * interpolation methods the transposed interpolation spreads each node onto
+ * its one or two grid cells, whose phases follow the spread.                 */
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar);
 
 /* The image spectrum before the inverse FFT: steps 1-3 of Algorithm 2.

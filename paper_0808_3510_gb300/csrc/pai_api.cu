@@ -806,7 +806,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // ---- tuner: the adjoint row kernel's CTA size, timed the same way ----------
   // (the spread's barriers and the forward's FFT passes favour different sizes)
   int threads_adj = threads;
-  if (tune && !method_interp(P->method)) {
+  if (tune) {
     int best_T = 0;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -853,8 +853,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       float adj_zf = 1e30f, adj_cufft = 1e30f;
-      const int nvariants = method_interp(P->method) ? 2 : 4;  // interpolation methods have no adjoint
-      for (int variant = 0; variant < nvariants; ++variant) {
+      for (int variant = 0; variant < 4; ++variant) {
         const bool adjoint = variant >= 2;
         P->zf = P->zf_adj = (variant % 2) == 0;
         float best = 1e30f;
@@ -965,7 +964,6 @@ pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f) {
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar) {
   if (!plan || !d_h || !d_pbar) return PAI_ERR_INVALID_ARG;
   if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
-  if (method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
   return run(plan, d_h, d_pbar, true);
 }
 
@@ -1077,7 +1075,6 @@ pai_status pai_host_wait(pai_plan_t plan) {
 
 pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, int reps, int adjoint, double* ms) {
   if (!plan || !d_in || !d_out || !ms || reps < 1) return PAI_ERR_INVALID_ARG;
-  if (adjoint && method_interp(plan->method)) return PAI_ERR_UNSUPPORTED;
   if (plan->qmode && !adjoint) return PAI_ERR_INVALID_ARG;  // a forward-model plan runs its adjoint pipeline
   int prev = 0;
   cudaGetDevice(&prev);

@@ -668,6 +668,24 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
 // Adjoint
 // ---------------------------------------------------------------------------
 
+// Adjoint of the node evaluation.  Windowed methods: the node record carries
+// e^{+i pi nu} (the transpose of the node's phase) and the taps weigh
+// w_t(fr).  Interpolation methods (H = 2 plans only): the phase belongs to the
+// grid cell, e^{+i pi nu_j}, applied to each cell after the spread, and tap
+// t = 1, 2 (cells j0, j0+1) weigh 1 - fr, fr (linear) or 1 on the nearer cell.
+template <int H>
+__device__ __forceinline__ float2 adj_node_phase(const RowProblem& P, int j0, float fr) {
+  if constexpr (H == 2) {
+    if (P.method >= PAI_METHOD_LINEAR) return make_float2(1.0f, 0.0f);
+  }
+  return node_phase(j0, fr, P.nt, P.M, P.nt_over_M);
+}
+
+__device__ __forceinline__ float interp_tap_weight(int method, int t, float fr) {
+  if (method == PAI_METHOD_NEAREST) return (t == 1) ? (fr >= 0.5f ? 0.0f : 1.0f) : (t == 2 ? (fr >= 0.5f ? 1.0f : 0.0f) : 0.0f);
+  return (t == 1) ? 1.0f - fr : (t == 2 ? fr : 0.0f);
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
@@ -746,17 +764,17 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
         if (nyq) {
           const float2 y = Zs[nzh];
           const float2 pb = make_float2(0.5f * wt * y.x, 0.5f * wt * y.y);
-          const float2 qp = cmul(pb, node_phase(j0p, frp, nt, M, P.nt_over_M));
-          const float2 qn = cmul(pb, node_phase(j0, fr, nt, M, P.nt_over_M));
+          const float2 qp = cmul(pb, adj_node_phase<H>(P, j0p, frp));
+          const float2 qn = cmul(pb, adj_node_phase<H>(P, j0, fr));
           N[nneg + nzh - 1] = make_float4(__int_as_float(j0p), frp, qp.x, qp.y);
           N[0] = make_float4(__int_as_float(j0), fr, qn.x, qn.y);
         } else if (!neg) {
           const float2 y = Zs[lp];
-          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), node_phase(j0p, frp, nt, M, P.nt_over_M));
+          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), adj_node_phase<H>(P, j0p, frp));
           N[nneg + lp - 1] = make_float4(__int_as_float(j0p), frp, q.x, q.y);
         } else {
           const float2 y = Zs[P.nz - lp];
-          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), node_phase(j0, fr, nt, M, P.nt_over_M));
+          const float2 q = cmul(make_float2(wt * y.x, wt * y.y), adj_node_phase<H>(P, j0, fr));
           N[nzh - lp] = make_float4(__int_as_float(j0), fr, q.x, q.y);
         }
       }
@@ -787,20 +805,20 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
             y.y -= y2.y;
           }
           const float2 pb = make_float2(0.5f * wt * y.x, 0.5f * wt * y.y);
-          const float2 php = node_phase(j0p, frp, nt, M, P.nt_over_M);
-          const float2 phn = node_phase(j0, fr, nt, M, P.nt_over_M);
+          const float2 php = adj_node_phase<H>(P, j0p, frp);
+          const float2 phn = adj_node_phase<H>(P, j0, fr);
           const float2 qp = cmul(pb, php), qn = cmul(pb, phn);
           N[nneg + nzh - 1] = make_float4(__int_as_float(j0p), frp, qp.x, qp.y);
           N[0] = make_float4(__int_as_float(j0), fr, qn.x, qn.y);
         } else if (!neg) {
           const float2 y = in1[lp];
           const float2 pb = make_float2(2.0f * wt * y.x, 2.0f * wt * y.y);
-          const float2 q = cmul(pb, node_phase(j0p, frp, nt, M, P.nt_over_M));
+          const float2 q = cmul(pb, adj_node_phase<H>(P, j0p, frp));
           N[nneg + lp - 1] = make_float4(__int_as_float(j0p), frp, q.x, q.y);
         } else {
           const float2 y = in2[lp];
           const float2 pb = make_float2(2.0f * wt * y.x, -2.0f * wt * y.y);
-          const float2 q = cmul(pb, node_phase(j0, fr, nt, M, P.nt_over_M));
+          const float2 q = cmul(pb, adj_node_phase<H>(P, j0, fr));
           N[nzh - lp] = make_float4(__int_as_float(j0), fr, q.x, q.y);
         }
       }
@@ -821,6 +839,7 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     // fixed order (chunk, tap, node): deterministic, no atomics.
     {
       const int CH = L.chunk;  // <= tpr
+      const bool interp = H == 2 && P.method >= PAI_METHOD_LINEAR;
       for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
       const int list_max = (P.nz >> 1) + (P.qmode ? 1 : 0);  // nodes per sign list, at most
       const int half_chunks = (list_max + CH - 1) / CH;         // uniform over the CTA's slots
@@ -855,8 +874,12 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
             // tap t = p (side 0) or 2H-1-p (side 1): w(z) = E_p(z^2) +- z O_p(z^2), z = fr - 1/2
+            const int t = side == 0 ? p : 2 * H - 1 - p;
             if (run > 0) {
-              const float w0 = side == 0 ? fmaf(z0, O0, E0) : fmaf(-z0, O0, E0);
+              float w0 = side == 0 ? fmaf(z0, O0, E0) : fmaf(-z0, O0, E0);
+              if constexpr (H == 2) {
+                if (interp) w0 = interp_tap_weight(P.method, t, nd0.y);
+              }
               float sx = w0 * nd0.z, sy = w0 * nd0.w;
               for (int r = 1; r < run; ++r) {
                 const float4 nd = N[c0 + lane + r];
@@ -868,11 +891,13 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
                   E = fmaf(E, z2, W.ce[p][e]);
                   O = fmaf(O, z2, W.co[p][e]);
                 }
-                const float w = fmaf(z, O, E);
+                float w = fmaf(z, O, E);
+                if constexpr (H == 2) {
+                  if (interp) w = interp_tap_weight(P.method, t, nd.y);
+                }
                 sx = fmaf(w, nd.z, sx);
                 sy = fmaf(w, nd.w, sy);
               }
-              const int t = side == 0 ? p : 2 * H - 1 - p;
               const int gi = PADI((j0 + t - H + 1) & mask);
               float2 x = X[gi];
               x.x += sx;
@@ -883,6 +908,11 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
           }
         }
       }
+    }
+    if constexpr (H == 2) {
+      // interpolation methods: the grid cells' phases e^{+i pi nu_j}
+      if (valid && P.method >= PAI_METHOD_LINEAR)
+        for (int g = lane; g < M; g += tpr) X[PADI(g)] = cmul(X[PADI(g)], node_phase(g, 0.0f, nt, M, P.nt_over_M));
     }
     __syncthreads();
     fft_smem<true, kLayoutFlat>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);

@@ -107,21 +107,33 @@ def test_mixed_methods_rejected(pai):
     assert e.value.status == 1  # PAI_ERR_INVALID_ARG
 
 
-def test_interpolation_has_no_adjoint(pai):
-    g = ph.Geometry(dim=2, nx=32, nt=64, nz=32)
-    plan = pai.Plan(gdict(g, method="nearest"))
-    with pytest.raises(pai.PAIError) as e:
-        plan.adjoint(to_gpu(ph.random_image(1, g)))
-    assert e.value.status == 2  # PAI_ERR_UNSUPPORTED
+@pytest.mark.parametrize("method", ["linear", "nearest"])
+def test_interpolation_adjoint_is_the_dense_transpose(pai, method):
+    """Tiny grid: the GPU adjoint against the transpose of the oracle's operator,
+    assembled column by column from unit data vectors."""
+    g = ph.Geometry(dim=2, nx=6, nt=32, nz=10, dz=0.9)
+    n = g.nx * g.nt
+    A = np.empty((g.nx * g.nz, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        A[:, i] = om.reconstruct(g, e.reshape(g.data_shape), method, 2.0).ravel()
+    h = ph.random_image(70, g).astype(np.float32)
+    plan = pai.Plan(gdict(g, method=method, oversampling=2))
+    got = to_np(plan.adjoint(to_gpu(h))).ravel()
+    assert rel(got, A.T @ h.astype(np.float64).ravel()) < TOL
 
 
+@pytest.mark.parametrize("method,c", [("tsinc", 2.0), ("linear", 2.0), ("nearest", 2.0), ("linear", 1.0),
+                                      ("nearest", 1.0)])
 @pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+                               ph.Geometry(dim=2, nx=300, nt=700, nz=350, dx=1.0, dt=0.5, c=1.5, dz=0.8),
                                ph.Geometry(dim=3, nx=32, ny=24, nt=64, nz=32, dz=0.8)],
-                         ids=["2d", "3d"])
-def test_tsinc_adjoint(pai, g, pipeline):
-    """The transposed spread with the sinc window: the dot-product identity
+                         ids=["2d", "2d-ragged", "3d"])
+def test_methods_adjoint_dot_product(pai, g, method, c, pipeline):
+    """The transposed spreads of the compared methods: the dot-product identity
     between the GPU forward and the GPU adjoint."""
-    plan = pai.Plan(gdict(g, method="tsinc", K=3))
+    plan = pai.Plan(gdict(g, method=method, oversampling=c, K=3 if method == "tsinc" else 0))
     p = ph.random_data(80, g)
     h = ph.random_image(81, g)
     Rp = to_np(plan.reconstruct(to_gpu(p)))
