@@ -40,10 +40,42 @@ namespace pai {
 
 #define PADI(i) ((i) + ((i) >> 5))
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex arithmetic on the packed two-lane FP32 instructions of sm_100+
+// (add/sub/mul/fma .rn.f32x2): one instruction per complex add, two per
+// complex product.  Each lane rounds exactly like its scalar counterpart.
+__device__ __forceinline__ unsigned long long pack2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(c)));
+  return unpack2(r);
+}
+// (a.x + i a.y)(b.x + i b.y) = a.x (b.x, b.y) + a.y (-b.y, b.x)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  return fma2(make_float2(a.x, a.x), b, mul2(make_float2(a.y, a.y), make_float2(-b.y, b.x)));
 }
 
 // cos and sin of 2 pi q / 16, q = 0..7
@@ -65,7 +97,7 @@ __device__ __forceinline__ float2 twq(float2 x) {
   if (Q == 4) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
   constexpr float c = cos16(Q);
   constexpr float s = INV ? sin16(Q) : -sin16(Q);
-  return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+  return fma2(make_float2(x.x, x.x), make_float2(c, s), mul2(make_float2(x.y, x.y), make_float2(-s, c)));
 }
 
 template <int R>
