@@ -285,6 +285,8 @@ def aggregate_over_ranks(ms_local: float, voxels_local: int, device=None):
 FORWARD_CONFIGS = {
     "forward3d": "3-D: 128^3 initial pressure (1-20 uniform balls) -> 128 x 128 detectors x 256 samples",
     "forward2d": "2-D: 2048 x 2048 initial pressure (50 f_circ discs) -> 2048 detectors x 4096 samples",
+    "datamodel2d": "2-D partial data g = w_cut Q f (Eq. data-part): forward2d with the cutoff eps = 16 fused into "
+                   "the copy of the detector rows",
 }
 
 
@@ -324,7 +326,7 @@ def run_forward_model(args, rank, world, local_rank):
                   oversampling=2.0, K=K)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    model = pai.ForwardModel(gdict_)
+    model = pai.ForwardModel(gdict_, cutoff=16.0 if args.config == "datamodel2d" else None)
     f = torch.from_numpy(img.astype(np.float32)).to(dev)
     out = torch.empty(g.data_shape, device=dev, dtype=torch.float32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
@@ -371,7 +373,8 @@ def run_forward_model(args, rank, world, local_rank):
                        f"oversampling 2, K = {K:g}", "voxels_per_step": g.voxels, "box": [bx, by, bz],
                        "l2": "flushed before every timed step (512 MiB write)", "parallelism": f"replicas x{world}"},
             "step": "forward model (image -> detector data)",
-            "parity": {"checked_by": "tests/test_gpu_forward.py", "bar_rel_l2": 1e-5},
+            "parity": {"checked_by": "tests/test_gpu_cutoff.py::test_data_model_against_oracle"
+                       if args.config == "datamodel2d" else "tests/test_gpu_forward.py", "bar_rel_l2": 1e-5},
             "roofline": {"bound": "hbm", "kernel": "row_adjoint in forward-model mode (node pairs, spread, inverse "
                          "FFT, crop)", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": peak_src, "algorithmic_bytes_per_launch": nbytes_alg,
@@ -383,6 +386,105 @@ def run_forward_model(args, rank, world, local_rank):
     model.close()
 
 
+# ---------------------------------------------------------------------------
+# the data cutoff w_cut (pai_cutoff): partial data g = w_cut * p
+# ---------------------------------------------------------------------------
+
+CUTOFF_DESC = ("2-D: w_cut (Eq. data-part) applied to 2048 detectors x 4096 samples of random data, eps = 16 "
+               "squared sampling steps (support radius 4 steps), out of place")
+
+
+def run_cutoff(args, rank, world, local_rank):
+    """One step = one out-of-place pai_cutoff over the 2-D large data grid
+    (33.6 MB read, 33.6 MB written); value = data samples per second over all
+    ranks.  The in-place call (only the samples within reach of a face are
+    rewritten) is timed beside it."""
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle of w_cut integrates the mollifier "
+                              "over each sample's own box; it is a checker, not a timed program"}))
+        return
+    import torch
+    import phantoms as ph
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+    from paper_0808_3510_gb300 import build as pai_build
+    if rank == 0 or world == 1:
+        pai_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_0808_3510_gb300 as pai
+    g = ph.Geometry(dim=2, nx=2048, nt=4096, nz=2048)
+    eps = 16.0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    plan = pai.Plan(dict(dim=2, nx=g.nx, nt=g.nt, nz=g.nz, K=4.0))
+    plan.set_cutoff(eps)
+    rng = np.random.default_rng(rank)
+    p = torch.from_numpy(rng.standard_normal((g.nx, g.nt)).astype(np.float32)).to(dev)
+    out = torch.empty_like(p)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    samples = g.nx * g.nt
+
+    def timed(fn, steps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i & 7))
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+
+    for _ in range(args.warmup):
+        plan.cutoff(p, out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    l0 = plan.kernel_launches
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ms = timed(lambda: plan.cutoff(p, out), args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    t1 = time.time()
+    launches = plan.kernel_launches - l0
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    ms_in_place = timed(lambda: plan.cutoff(p, p), min(args.steps, 200))
+    ms_max, value = aggregate_over_ranks(ms, samples, dev)
+    nbytes_alg = samples * 8
+    peak, peak_src = hbm_peak()
+    achieved = nbytes_alg / (ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "data samples/s through w_cut", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cutoff2d: {CUTOFF_DESC}", "samples_per_step": samples, "eps": eps,
+                       "l2": "flushed before every timed step (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "step": "data cutoff (pai_cutoff, out of place)",
+            "parity": {"checked_by": "tests/test_gpu_cutoff.py::test_cutoff_full_size_sampled",
+                       "bar": "2.5e-7 relative per sample"},
+            "roofline": {"bound": "hbm", "kernel": "cutoff_kernel (one streaming pass)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": nbytes_alg, "kernel_ms": ms},
+            "in_place_ms": ms_in_place,
+            "cpu_baseline": None, "e2e": {"value": None, "unit": "samples/s", "note": "no host-memory entry point"},
+            "gpu_launches": launches, "clocks": clocks, "wall_s_timed_region": t1 - t0,
+        }))
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +492,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="large2d", choices=["large2d", "plain2d", "planar3d", "adjoint3d",
-                                                            "batched2d", "frames2d", "forward3d", "forward2d"])
+                                                            "batched2d", "frames2d", "forward3d", "forward2d",
+                                                            "datamodel2d", "cutoff2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -402,6 +505,8 @@ def main():
 
     if args.config in FORWARD_CONFIGS:
         return run_forward_model(args, rank, world, local_rank)
+    if args.config == "cutoff2d":
+        return run_cutoff(args, rank, world, local_rank)
 
     if args.impl == "reference":
         if rank != 0:

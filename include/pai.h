@@ -259,6 +259,49 @@ pai_status pai_forward_model(pai_plan_t plan, const float* d_f, float* d_p);
 /* Box extents of a forward-model plan (by = 1 in 2-D).                       */
 pai_status pai_forward_box(pai_plan_t plan, int* bx, int* by, int* bz);
 
+/* Smooth cutoff of the data (Eq. data-part, Sec. 2; built as in Sec. 5):
+ * partial (limited-view) data are g = w_cut * (Q f), the complete data times
+ * a smooth nonnegative weight that is one well inside the measured region
+ * and falls to zero at its edges.
+ *
+ * Definition.  Positions are measured in sampling steps along every data
+ * axis (lateral axes in units of dx (dy), time in units of dt); the data grid
+ * [nx] ([ny]) [nt] spans the box [0, n_a] on axis a, its samples sitting at
+ * 0 .. n_a - 1.  The mollifier is phi(v) = C exp(-1 / (1 - |v|^2/eps)^4) for
+ * |v|^2 < eps, zero elsewhere, C making its integral one (the support and
+ * exponent of Sec. 5, written scale-free; eps is in squared sampling steps,
+ * the support radius sqrt(eps) steps).  w_cut(u) = integral of
+ * phi(v) chi_box(u - v) dv.  A sample whose distances to the lower and upper
+ * faces of axis a are s_a = min(u_a, n_a - u_a) has the weight
+ * T[s_1]..[s_d] with every s_a clipped to R = ceil(sqrt(eps)) (beyond that
+ * distance the face does not reach the mollifier); the (R+1)^d table is
+ * computed on the host by Gauss-Legendre quadrature (error below 1e-9).
+ *
+ * pai_cutoff_table: host only, no device work.  dim 2 or 3; 1 <= eps <= 256.
+ * Writes R to *R (may be NULL) and, when table != NULL and capacity >=
+ * (R+1)^dim, the weights, index ((s_x (R+1) + s_y) (R+1) + s_t) in 3-D and
+ * s_x (R+1) + s_t in 2-D; a smaller capacity returns PAI_ERR_INVALID_ARG
+ * after writing *R.
+ *
+ * pai_set_cutoff: attaches the cutoff with parameter eps to a single-problem
+ * plan (reconstruction or forward model); eps = 0 removes it.  Requires
+ * 1 <= eps <= 256 and every data axis n_a >= 2 ceil(sqrt(eps)) (so each
+ * sample is within reach of at most one face per axis), else
+ * PAI_ERR_INVALID_ARG; batched plans return PAI_ERR_UNSUPPORTED.  Computes
+ * the table, uploads it into plan-owned device memory and waits for the
+ * upload.  A forward-model plan with a cutoff returns w_cut * (Q f) from
+ * pai_forward_model: the weight is applied by the kernel that copies the
+ * detector rows out of the box, at no extra memory traffic.
+ *
+ * pai_cutoff: d_out = w_cut * d_in over the plan's data grid [nx][ny][nt]
+ * (device FP32, contiguous).  d_in == d_out (in place) touches only the
+ * samples whose weight differs from one; partially overlapping buffers are
+ * not allowed.  PAI_ERR_INVALID_ARG without a cutoff set.  Asynchronous on
+ * the plan's stream.                                                         */
+pai_status pai_cutoff_table(int dim, double eps, double* table, int capacity, int* R);
+pai_status pai_set_cutoff(pai_plan_t plan, double eps);
+pai_status pai_cutoff(pai_plan_t plan, const float* d_in, float* d_out);
+
 /* Size of the static device scratch array used by pai_spectrum_rows_noalloc. */
 #define PAI_NOALLOC_SCRATCH_BYTES (1u << 20)
 

@@ -23,8 +23,8 @@ from typing import Iterable, List, Optional, Sequence
 
 import torch
 
-__all__ = ["Plan", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "library_path", "load_library", "geometry",
-           "window_probe"]
+__all__ = ["Plan", "ForwardModel", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "library_path", "load_library",
+           "geometry", "window_probe", "cutoff_table"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libpai.so")
@@ -140,6 +140,12 @@ def load_library() -> ctypes.CDLL:
         lib.pai_window_probe.restype = st
         lib.pai_spectrum_rows_noalloc.argtypes = [G, fp, fp, vp]
         lib.pai_spectrum_rows_noalloc.restype = st
+        lib.pai_cutoff_table.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int, ip]
+        lib.pai_cutoff_table.restype = st
+        lib.pai_set_cutoff.argtypes = [vp, ctypes.c_double]
+        lib.pai_set_cutoff.restype = st
+        lib.pai_cutoff.argtypes = [vp, fp, fp]
+        lib.pai_cutoff.restype = st
         lib.pai_status_string.argtypes = [st]
         lib.pai_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -185,6 +191,40 @@ def window_probe(H: int, beta: float, c: float, y=()):
     pe, fe = ctypes.c_double(), ctypes.c_double()
     _check(lib.pai_window_probe(H, beta, c, n, ya, out, ctypes.byref(pe), ctypes.byref(fe)), "pai_window_probe")
     return [out[i] for i in range(n)], pe.value, fe.value
+
+
+def cutoff_table(dim: int, eps: float):
+    """The weights of the data cutoff w_cut (``pai_cutoff_table``, host only) as a
+    nested list of shape (R+1,)*dim indexed by the clipped distances to the
+    faces (time last), and R."""
+    lib = load_library()
+    R = ctypes.c_int()
+    _check(lib.pai_cutoff_table(int(dim), float(eps), None, 0, ctypes.byref(R)), "pai_cutoff_table")
+    n = (R.value + 1) ** dim
+    buf = (ctypes.c_double * n)()
+    _check(lib.pai_cutoff_table(int(dim), float(eps), buf, n, ctypes.byref(R)), "pai_cutoff_table")
+    flat = list(buf)
+    r1 = R.value + 1
+    if dim == 2:
+        return [flat[i * r1:(i + 1) * r1] for i in range(r1)], R.value
+    return [[flat[(i * r1 + j) * r1:(i * r1 + j + 1) * r1] for j in range(r1)] for i in range(r1)], R.value
+
+
+def _apply_cutoff(obj, p: torch.Tensor, out: Optional[torch.Tensor]) -> torch.Tensor:
+    g = obj.geom if isinstance(obj, ForwardModel) else obj.geoms[0]
+    n = _numel(g, g.nt)
+    for t, what in ((p, "p"), (out, "out")):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.device != obj.device or t.dtype != torch.float32
+                              or not t.is_contiguous() or t.numel() != n):
+            raise ValueError(f"{what} must be a contiguous float32 tensor on {obj.device} with {n} elements")
+    if out is None:
+        out = torch.empty(_shape(g, g.nt), device=obj.device, dtype=torch.float32)
+    cur = torch.cuda.current_stream(obj.device).cuda_stream
+    if cur != obj._stream:
+        _check(obj._lib.pai_set_stream(obj._h, ctypes.c_void_p(cur)), "pai_set_stream")
+        obj._stream = cur
+    _check(obj._lib.pai_cutoff(obj._h, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(out.data_ptr())), "pai_cutoff")
+    return out
 
 
 def spectrum_rows_noalloc(g, pt: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
@@ -342,6 +382,14 @@ class Plan:
                                             int(reps), 1 if adjoint else 0, ms), "pai_profile_stages")
         return [ms[0], ms[1], ms[2]]
 
+    def set_cutoff(self, eps: float):
+        """Attach the data cutoff w_cut with parameter eps (squared sampling steps; 0 removes it)."""
+        _check(self._lib.pai_set_cutoff(self._h, float(eps)), "pai_set_cutoff")
+
+    def cutoff(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """w_cut * p over the data grid (``pai_cutoff``); out may be p itself."""
+        return _apply_cutoff(self, p, out)
+
     # -- introspection ------------------------------------------------------
     @property
     def info(self) -> dict:
@@ -373,7 +421,7 @@ class ForwardModel:
     exactly for its trigonometric interpolant in a zero-padded periodic box.
     Calls run on torch's current stream."""
 
-    def __init__(self, g, stream: Optional[torch.cuda.Stream] = None):
+    def __init__(self, g, stream: Optional[torch.cuda.Stream] = None, cutoff: Optional[float] = None):
         lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("paper_0808_3510_gb300 needs a CUDA device")
@@ -389,6 +437,16 @@ class ForwardModel:
         b = [ctypes.c_int() for _ in range(3)]
         _check(lib.pai_forward_box(h, *[ctypes.byref(v) for v in b]), "pai_forward_box")
         self.box = tuple(v.value for v in b)
+        if cutoff:
+            self.set_cutoff(cutoff)
+
+    def set_cutoff(self, eps: float):
+        """Return w_cut * (Q f) from now on (the data model of partial data); 0 removes the cutoff."""
+        _check(self._lib.pai_set_cutoff(self._h, float(eps)), "pai_set_cutoff")
+
+    def cutoff(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """w_cut * p over the detector data grid (``pai_cutoff``); out may be p itself."""
+        return _apply_cutoff(self, p, out)
 
     def __call__(self, f: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         g = self.geom

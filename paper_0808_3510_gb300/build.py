@@ -27,6 +27,7 @@ UNITS = [
     ("pai_plan_math.cpp", [], "pai_plan_math.o"),
     ("pai_noalloc.cu", [], "pai_noalloc.o"),
     ("pai_lateral.cu", [], "pai_lateral.o"),
+    ("pai_cutoff.cu", [], "pai_cutoff.o"),
     ("pai_row_inst.cu", ["-DPAI_HLO=2", "-DPAI_HHI=4"], "pai_row_h2.o"),
     ("pai_row_inst.cu", ["-DPAI_HLO=5", "-DPAI_HHI=6"], "pai_row_h5.o"),
     ("pai_row_inst.cu", ["-DPAI_HLO=7", "-DPAI_HHI=8"], "pai_row_h7.o"),

@@ -108,6 +108,10 @@ struct pai_plan_s {
   pai_geometry qimg{};
   float* d_qin = nullptr;   // box image
   float* d_qout = nullptr;  // box data
+  // data cutoff w_cut (pai_set_cutoff): weight table on the device
+  float* d_cut = nullptr;
+  int cut_R = 0;
+  double cut_eps = 0.0;
   bool use_graph = true;
   std::vector<GraphEntry> graphs;
   long long own_kernels = 0, fft_execs = 0;
@@ -213,6 +217,7 @@ void release(pai_plan_s* P) {
   if (P->s_down) cudaStreamSynchronize(P->s_down);
   cudaFree(P->d_qin);
   cudaFree(P->d_qout);
+  cudaFree(P->d_cut);
   for (int k = 0; k < 2; ++k) {
     cudaFree(P->d_pipe_in[k]);
     cudaFree(P->d_pipe_out[k]);
@@ -943,6 +948,9 @@ int forward_box_extent(int n, double d, const pai_geometry& g) {
 
 }  // namespace
 
+// the detector data grid of a single-problem plan: [nx][ny][nt]
+static const pai_geometry& data_geometry(pai_plan_t plan) { return plan->qmode ? plan->qimg : plan->probs[0].g; }
+
 extern "C" {
 
 pai_status pai_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out) {
@@ -1221,13 +1229,90 @@ pai_status pai_forward_model(pai_plan_t plan, const float* d_f, float* d_p) {
   pad_box_kernel<<<blocks, 256, 0, plan->stream>>>(d_f, plan->d_qin, gi.nx, ny, gi.nz, by, gb.nz, total);
   pai_status st = cuda_status(cudaGetLastError());
   if (st == PAI_OK) st = run(plan, plan->d_qin, plan->d_qout, true);
-  if (st == PAI_OK) {
+  if (st == PAI_OK && plan->d_cut) {
+    // the data model g = w_cut * (Q f): the weight applied while the detector rows leave the box
+    CutoffLaunch a{plan->d_qout, d_p, plan->d_cut, gi.nx, ny, gi.nt, by, plan->cut_R, gi.dim};
+    st = cuda_status(launch_cutoff(a, plan->stream, sms));
+    if (st == PAI_OK) plan->own_kernels += 1;
+  } else if (st == PAI_OK) {
     // detectors x < nx (and y < ny) of the box data [bx][by][nt]
     const size_t row = (size_t)ny * gi.nt * sizeof(float), pitch = (size_t)by * gi.nt * sizeof(float);
     st = cuda_status(cudaMemcpy2DAsync(d_p, row, plan->d_qout, pitch, row, gi.nx, cudaMemcpyDeviceToDevice,
                                        plan->stream));
   }
   if (st == PAI_OK) plan->own_kernels += 1;  // the pad kernel (the rest is counted by run)
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_cutoff_table(int dim, double eps, double* table, int capacity, int* R) {
+  if ((dim != 2 && dim != 3) || !(eps >= 1.0 && eps <= 256.0)) return PAI_ERR_INVALID_ARG;
+  const int r = cutoff_radius(eps);
+  if (R) *R = r;
+  if (!table) return PAI_OK;
+  long long n = 1;
+  for (int a = 0; a < dim; ++a) n *= r + 1;
+  if (capacity < n) return PAI_ERR_INVALID_ARG;
+  std::vector<double> w;
+  cutoff_table(dim, eps, w);
+  std::copy(w.begin(), w.end(), table);
+  return PAI_OK;
+}
+
+pai_status pai_set_cutoff(pai_plan_t plan, double eps) {
+  if (!plan) return PAI_ERR_INVALID_ARG;
+  if (plan->probs.size() != 1) return PAI_ERR_UNSUPPORTED;
+  const pai_geometry& g = data_geometry(plan);
+  if (eps != 0.0) {
+    if (!(eps >= 1.0 && eps <= 256.0)) return PAI_ERR_INVALID_ARG;
+    const int R = cutoff_radius(eps);
+    const int ny = g.dim == 3 ? g.ny : 2 * R;
+    if (g.nx < 2 * R || ny < 2 * R || g.nt < 2 * R) return PAI_ERR_INVALID_ARG;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = cuda_status(cudaStreamSynchronize(plan->stream));
+  if (st == PAI_OK) {
+    cudaFree(plan->d_cut);
+    plan->d_cut = nullptr;
+    plan->cut_R = 0;
+    plan->cut_eps = 0.0;
+  }
+  if (st == PAI_OK && eps != 0.0) {
+    std::vector<double> w;
+    cutoff_table(g.dim, eps, w);
+    std::vector<float> wf(w.begin(), w.end());
+    float* d = nullptr;
+    st = cuda_status(cudaMalloc(&d, wf.size() * sizeof(float)));
+    if (st == PAI_OK) st = cuda_status(cudaMemcpy(d, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (st == PAI_OK) {
+      plan->d_cut = d;
+      plan->cut_R = cutoff_radius(eps);
+      plan->cut_eps = eps;
+    } else {
+      cudaFree(d);
+    }
+  }
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_cutoff(pai_plan_t plan, const float* d_in, float* d_out) {
+  if (!plan || !d_in || !d_out || !plan->d_cut) return PAI_ERR_INVALID_ARG;
+  const pai_geometry& g = data_geometry(plan);
+  const int ny = g.dim == 3 ? g.ny : 1;
+  const size_t bytes = (size_t)g.nx * ny * g.nt * sizeof(float);
+  const char *a = reinterpret_cast<const char*>(d_in), *b = reinterpret_cast<const char*>(d_out);
+  if (a != b && a < b + bytes && b < a + bytes) return PAI_ERR_INVALID_ARG;  // partial overlap
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+  CutoffLaunch la{d_in, d_out, plan->d_cut, g.nx, ny, g.nt, ny, plan->cut_R, g.dim};
+  pai_status st = cuda_status(launch_cutoff(la, plan->stream, sms));
+  if (st == PAI_OK) plan->own_kernels += 1;
   if (prev != plan->device) cudaSetDevice(prev);
   return st;
 }

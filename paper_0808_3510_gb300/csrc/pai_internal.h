@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/pai.h"
 
 namespace pai {
@@ -135,5 +137,18 @@ cudaError_t launch_lateral_c2c(const float2* in, float2* out, int L, int C, int 
 cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const float2* tw, int twstride,
                             cudaStream_t s);
 int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H, bool zf = false);
+
+// Data cutoff w_cut (pai_cutoff.cu).  R = ceil(sqrt(eps)); the table holds
+// (R+1)^dim weights indexed by the clipped distances to the faces, time last.
+int cutoff_radius(double eps);
+void cutoff_table(int dim, double eps, std::vector<double>& out);
+struct CutoffLaunch {
+  const float* in;     // input row (x, y) at (x * in_ny + y) * nt
+  float* out;          // output row (x, y) at (x * ny + y) * nt
+  const float* table;  // device, (R+1)^dim weights
+  int nx, ny, nt, in_ny;
+  int R, dim;
+};
+cudaError_t launch_cutoff(const CutoffLaunch& a, cudaStream_t stream, int sms);
 
 }  // namespace pai

@@ -138,3 +138,39 @@ def test_forward_plan_host_validation(pai):
     assert lib.pai_forward_model(None, None, None) == 1
     bx = ctypes.c_int()
     assert lib.pai_forward_box(None, ctypes.byref(bx), ctypes.byref(bx), ctypes.byref(bx)) == 1
+
+
+@pytest.mark.parametrize("dim,eps", [(2, 1.0), (2, 16.0), (2, 30.25), (3, 4.0), (3, 9.0), (3, 20.0)])
+def test_cutoff_table_matches_the_oracle(pai, dim, eps):
+    """The plan-time weight table of the data cutoff (host quadrature in the
+    library) against the oracle's w_cut at the samples with those distances to
+    the faces (the oracle integrates over each sample's own box)."""
+    import numpy as np
+
+    import oracle.cutoff as oc
+    T, R = pai.cutoff_table(dim, eps)
+    assert R == math.ceil(math.sqrt(eps) - 1e-12)
+    T = np.array(T)
+    big = 4 * R + 8
+    shape = (big,) * dim
+    w = oc.weights(shape, eps)
+    for idx in np.ndindex(*T.shape):
+        assert abs(T[idx] - w[idx]) < 1e-12, (idx, T[idx], w[idx])
+        # the upper faces: distance s from n_a lies at index n_a - s
+        up = tuple(big - s if s > 0 else 0 for s in idx)
+        assert abs(T[idx] - w[up]) < 1e-12
+
+
+def test_cutoff_host_validation(pai):
+    lib = pai.load_library()
+    R = ctypes.c_int(-5)
+    assert lib.pai_cutoff_table(4, 4.0, None, 0, ctypes.byref(R)) == 1
+    assert lib.pai_cutoff_table(2, 0.5, None, 0, ctypes.byref(R)) == 1
+    assert lib.pai_cutoff_table(2, 257.0, None, 0, ctypes.byref(R)) == 1
+    assert lib.pai_cutoff_table(2, float("nan"), None, 0, ctypes.byref(R)) == 1
+    buf = (ctypes.c_double * 8)()
+    assert lib.pai_cutoff_table(2, 4.0, buf, 8, ctypes.byref(R)) == 1 and R.value == 2   # needs 9
+    buf9 = (ctypes.c_double * 9)()
+    assert lib.pai_cutoff_table(2, 4.0, buf9, 9, ctypes.byref(R)) == 0 and buf9[8] == 1.0 and abs(buf9[0] - 0.25) < 1e-11
+    assert lib.pai_set_cutoff(None, 4.0) == 1
+    assert lib.pai_cutoff(None, None, None) == 1

@@ -1,0 +1,161 @@
+"""The data cutoff w_cut (Eq. data-part, Sec. 5) on the GPU: pai_cutoff and the
+data model g = w_cut * (Q f) of a forward-model plan, against the FP64 oracle
+(oracle/cutoff.py).
+
+Bar: every sample within 2.5e-7 relative of the oracle's w_cut * p (one FP32
+rounding of the weight and one of the product); composed with the forward model
+or the reconstruction, relative L2 <= 1e-5 as everywhere else.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.cutoff as oc
+import phantoms as ph
+from gpu_common import TOL, gdict, pai, rel, to_gpu, to_np  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+ELEM_TOL = 2.5e-7
+
+
+def _check_elementwise(got, ref):
+    got = np.asarray(got, np.float64).reshape(ref.shape)
+    err = np.abs(got - ref)
+    assert np.all(err <= ELEM_TOL * np.abs(ref) + 1e-30), float(np.max(err / (np.abs(ref) + 1e-30)))
+
+
+CASES = [
+    (ph.Geometry(dim=2, nx=40, nt=64, nz=32), 16.0),              # float4 rows
+    (ph.Geometry(dim=2, nx=34, nt=70, nz=32, dt=0.5), 9.0),       # nt % 4 = 2: float2 rows
+    (ph.Geometry(dim=2, nx=8, nt=8, nz=8), 16.0),                 # the smallest grid eps allows: 2R = 8
+    (ph.Geometry(dim=2, nx=2, nt=2, nz=2), 1.0),                  # R = 1
+    (ph.Geometry(dim=3, nx=12, ny=10, nt=24, nz=8), 4.0),
+    (ph.Geometry(dim=3, nx=18, ny=16, nt=40, nz=16, dy=1.2), 16.0),
+    (ph.Geometry(dim=3, nx=10, ny=12, nt=30, nz=8), 20.25),       # sqrt(eps) = 4.5: R = 5
+]
+
+
+@pytest.mark.parametrize("g,eps", CASES, ids=lambda v: str(v) if isinstance(v, float) else
+                         f"{v.dim}d-{v.nx}x{v.ny}x{v.nt}")
+def test_cutoff_matches_the_oracle(pai, g, eps):
+    plan = pai.Plan(gdict(g))
+    plan.set_cutoff(eps)
+    p = ph.random_data(51, g).astype(np.float32)
+    got = to_np(plan.cutoff(to_gpu(p)))
+    _check_elementwise(got, oc.apply(p.astype(np.float64), eps))
+
+
+def test_cutoff_in_place_and_unaligned(pai):
+    """In place (only samples with weight below one are rewritten) and from a
+    buffer 4 bytes off a 16-byte boundary (scalar rows): the same values."""
+    import torch
+    g = ph.Geometry(dim=3, nx=16, ny=12, nt=36, nz=8)
+    eps = 9.0
+    plan = pai.Plan(gdict(g))
+    plan.set_cutoff(eps)
+    p = ph.random_data(52, g).astype(np.float32)
+    ref = oc.apply(p.astype(np.float64), eps)
+    x = to_gpu(p)
+    out_of_place = plan.cutoff(x)
+    y = x.clone()
+    plan.cutoff(y, out=y)
+    assert torch.equal(y, out_of_place)
+    _check_elementwise(to_np(y), ref)
+    buf = torch.zeros(p.size + 1, device="cuda")
+    buf[1:].copy_(x.reshape(-1))
+    xs = buf[1:]
+    assert xs.data_ptr() % 16 == 4
+    out = torch.empty_like(xs)
+    plan.cutoff(xs, out=out)
+    assert torch.equal(out.reshape(out_of_place.shape), out_of_place)
+
+
+def test_cutoff_full_size_sampled(pai):
+    """2048 x 4096 (the 2-D large data grid), eps = 16: the band along every
+    face and random interior samples against the oracle, sample by sample."""
+    g = ph.Geometry(dim=2, nx=2048, nt=4096, nz=2048)
+    eps = 16.0
+    plan = pai.Plan(gdict(g, K=4))
+    plan.set_cutoff(eps)
+    rng = np.random.default_rng(53)
+    p = rng.standard_normal((g.nx, g.nt)).astype(np.float32)
+    got = to_np(plan.cutoff(to_gpu(p)))
+    xs = list(range(0, 6)) + list(range(g.nx - 6, g.nx)) + rng.integers(0, g.nx, 20).tolist()
+    ts = list(range(0, 6)) + list(range(g.nt - 6, g.nt)) + rng.integers(0, g.nt, 20).tolist()
+    for x in xs:
+        for t in ts:
+            w = oc.weight_at((float(x), float(t)), (g.nx, g.nt), eps)
+            ref = float(p[x, t]) * w
+            assert abs(got[x, t] - ref) <= ELEM_TOL * abs(ref) + 1e-30, (x, t)
+    # rows away from every face are untouched
+    assert np.array_equal(got[8:-8, 8:-8], p[8:-8, 8:-8].astype(np.float64))
+
+
+@pytest.mark.parametrize("g,eps", [(ph.Geometry(dim=2, nx=32, nt=64, nz=24), 16.0),
+                                   (ph.Geometry(dim=2, nx=50, nt=90, nz=36, dx=0.8, dt=0.5, c=1.3, dz=1.1), 9.0),
+                                   (ph.Geometry(dim=3, nx=24, ny=16, nt=32, nz=20), 4.0)],
+                         ids=["2d", "2d-general", "3d"])
+def test_data_model_against_oracle(pai, g, eps):
+    """g = w_cut * (Q f): the forward-model plan with a cutoff equals the oracle's
+    forward model times the oracle's weights, and bit for bit the plain model
+    followed by pai_cutoff."""
+    import torch
+    img = ph.random_image(91, g).astype(np.float32)
+    model = pai.ForwardModel(gdict(g, K=3), cutoff=eps)
+    got = model(to_gpu(img))
+    ref = oracle.forward_model(g, img.astype(np.float64)) * oc.weights(g.data_shape, eps)
+    assert rel(to_np(got), ref) < TOL
+    plain = pai.ForwardModel(gdict(g, K=3))
+    q = plain(to_gpu(img))
+    plain.set_cutoff(eps)
+    assert torch.equal(plain.cutoff(q), got)
+
+
+def test_limited_view_reconstruction_against_oracle(pai):
+    """The limited-view study of Sec. 2: the exact inverse applied to partial
+    data, f_dagger = R (w_cut Q f), on the GPU end to end against the oracle's
+    chain; the cut data lose the object's image near the lateral edges."""
+    g = ph.Geometry(dim=2, nx=64, nt=128, nz=64)
+    eps = 64.0
+    img = np.zeros((g.nx, g.nz), np.float32)
+    img[30:36, 20:26] = 1.0          # a square in the middle of the aperture
+    img[1:5, 40:44] = 1.0            # and one at the lateral edge
+    model = pai.ForwardModel(gdict(g, K=3), cutoff=eps)
+    plan = pai.Plan(gdict(g, K=3))
+    f_dag = to_np(plan.reconstruct(model(to_gpu(img))))
+    data_ref = oracle.forward_model(g, img.astype(np.float64)) * oc.weights((g.nx, g.nt), eps)
+    f_ref = oracle.reconstruct(g, data_ref)
+    assert rel(f_dag, f_ref) < TOL
+    full = to_np(plan.reconstruct(pai.ForwardModel(gdict(g, K=3))(to_gpu(img))))
+    mid = (slice(28, 38), slice(18, 28))
+    edge = (slice(0, 7), slice(38, 46))
+    d_mid = np.linalg.norm(f_dag[mid] - full[mid]) / np.linalg.norm(full[mid])
+    d_edge = np.linalg.norm(f_dag[edge] - full[edge]) / np.linalg.norm(full[edge])
+    assert d_edge > 1.5 * d_mid and d_mid < 0.05, (d_mid, d_edge)   # oracle: 0.020 and 0.047
+
+
+def test_cutoff_validation(pai):
+    import ctypes
+
+    import torch
+    g = ph.Geometry(dim=2, nx=16, nt=32, nz=16)
+    plan = pai.Plan(gdict(g))
+    x = torch.zeros(16 * 32, device="cuda")
+    lib = pai.load_library()
+    # no cutoff set yet
+    assert lib.pai_cutoff(plan._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr())) == 1
+    with pytest.raises(pai.PAIError):
+        plan.set_cutoff(0.5)
+    with pytest.raises(pai.PAIError):
+        plan.set_cutoff(81.0)          # 2 ceil(9) = 18 > nx = 16
+    plan.set_cutoff(64.0)              # 2 * 8 = 16 fits
+    # partially overlapping buffers
+    big = torch.zeros(16 * 32 + 64, device="cuda")
+    assert lib.pai_cutoff(plan._h, ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(big[64:].data_ptr())) == 1
+    plan.set_cutoff(0.0)
+    assert lib.pai_cutoff(plan._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr())) == 1
+    batch = pai.Plan([gdict(g), gdict(g)])
+    with pytest.raises(pai.PAIError) as e:
+        batch.set_cutoff(4.0)
+    assert e.value.status == 2
