@@ -306,6 +306,39 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
   constexpr int R = 16;
   float2 v[R];
   const int MR = M / R, mask = M - 1, h = nt >> 1;
+  if (M == 2 * nt) {
+    // Oversampling 2: only the inputs r = 0..3 and 12..15 hold samples (the
+    // others fall in the zero padding), a block b_s, s = -4..3, of 8 values.
+    // With w = e^{-2 pi i/16}: X[2m] = sum_s b_s w^{2sm} and
+    // X[2m+1] = sum_s (b_s w^s) w^{2sm}, two length-8 DFTs.
+    float2 c8[8], d8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = q < 4 ? q : q + 8;
+      const int n = (lane + r * MR + h) & mask;
+      const float2 g = __ldg(&src[n]);
+      const float s = __ldg(&prescale[n]);
+      c8[q] = make_float2(s * g.x, s * g.y);
+    }
+    d8[0] = c8[0];
+    d8[1] = twq<1, false>(c8[1]);
+    d8[2] = twq<2, false>(c8[2]);
+    d8[3] = twq<3, false>(c8[3]);
+    d8[4] = twq<4, true>(c8[4]);  // w^-4 = i
+    d8[5] = twq<3, true>(c8[5]);
+    d8[6] = twq<2, true>(c8[6]);
+    d8[7] = twq<1, true>(c8[7]);
+    dft_reg<8, false>(c8);
+    dft_reg<8, false>(d8);
+    float2* dst = X + PADI(lane * R);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      dst[2 * m] = c8[m];
+      dst[2 * m + 1] = d8[m];
+    }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int m = lane + r * MR;
