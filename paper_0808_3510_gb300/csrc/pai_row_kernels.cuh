@@ -379,6 +379,89 @@ __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane,
   else if (rem == 1) fft_pass<2, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
 }
 
+// Inverse length-M transform of an adjoint row with the crop fused: the
+// passes run remainder radix first and radix 16 last, and the last pass
+// (Ns = M/16, butterfly j = lane, outputs at positions m = j + r M/16) writes
+// the outputs that hold samples n = (m + nt/2) mod M < nt, times
+// s_n = scale * prescale[n], straight to dst[n].  At oversampling 2
+// (M = 2 nt) only r = 0..3 (n = m + M/4) and r = 12..15 (n = m - 3M/4) are
+// kept, and only those 8 outputs are computed: with w = e^{+2 pi i/16},
+// A = inverse DFT8 of the even inputs and B of the odd,
+// Y[t] = A[t] + w^t B[t] (t = 0..3) and Y[t+8] = A[t] - w^t B[t] (t = 4..7).
+__device__ __forceinline__ void fft_inverse_crop(float2* X, int M, int mshift, int nt, int lane, int tpr,
+                                                 const float2* __restrict__ tw, int twstride, float2* dst,
+                                                 const float* __restrict__ prescale, float scale, bool valid) {
+  int Ns = 1;
+  const int r0 = mshift & 3;
+  if (r0 == 3) {
+    fft_pass<8, true, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
+    Ns = 8;
+  } else if (r0 == 2) {
+    fft_pass<4, true, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
+    Ns = 4;
+  } else if (r0 == 1) {
+    fft_pass<2, true, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
+    Ns = 2;
+  }
+  while (Ns * 16 < M) {
+    fft_pass<16, true, kLayoutPadded>(X, M, Ns, lane, tpr, tw, twstride);
+    Ns <<= 4;
+  }
+  if (!valid) return;
+  const int j = lane;
+  float2 v[16];
+  if ((Ns & 31) == 0) {
+    const float2* src = X + PADI(j);
+    const int rs = Ns + (Ns >> 5);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = src[r * rs];
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = X[PADI(j + r * Ns)];
+  }
+  if (Ns > 1) {
+    TwBase<16> tb;
+    tw_load<16>(tb, tw, j * twstride);
+    tw_apply<16, true>(v, tb);
+  }
+  const int q4 = M >> 2;
+  if (M == 2 * nt) {
+    float2 a[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      a[q] = v[2 * q];
+      b[q] = v[2 * q + 1];
+    }
+    dft_reg<8, true>(a);
+    dft_reg<8, true>(b);
+    b[1] = twq<1, true>(b[1]);
+    b[2] = twq<2, true>(b[2]);
+    b[3] = twq<3, true>(b[3]);
+    b[4] = twq<4, true>(b[4]);
+    b[5] = twq<5, true>(b[5]);
+    b[6] = twq<6, true>(b[6]);
+    b[7] = twq<7, true>(b[7]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 y = q < 4 ? cadd(a[q], b[q]) : csub(a[q], b[q]);
+      const int n = q < 4 ? j + q * Ns + q4 : j + (q + 8) * Ns - 3 * q4;
+      const float s = scale * __ldg(&prescale[n]);
+      dst[n] = make_float2(s * y.x, s * y.y);
+    }
+    return;
+  }
+  dft_reg<16, true>(v);
+  const int mask = M - 1, h = nt >> 1;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int n = (j + r * Ns + h) & mask;
+    if (n < nt) {
+      const float s = scale * __ldg(&prescale[n]);
+      dst[n] = make_float2(s * v[r].x, s * v[r].y);
+    }
+  }
+}
+
 // Length-M FFT (M = 2^mshift >= 32) of a padded row slot, in shared memory;
 // the last pass writes layout OUT.
 // Threads with active == false take part in the barriers only (used when a
@@ -980,17 +1063,9 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
         for (int g = lane; g < M; g += tpr) X[PADI(g)] = cmul(X[PADI(g)], node_phase(g, 0.0f, nt, M, P.nt_over_M));
     }
     __syncthreads();
-    fft_smem<true, kLayoutFlat>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
-    if (valid) {
-      const float scale = (!ZF && rg.mirror) ? 0.5f : 1.0f;
-      float2* dst = const_cast<float2*>(P.pt) + (size_t)row * nt;
-      const int h = nt >> 1;
-      for (int n = lane; n < nt; n += tpr) {
-        const float2 v = X[(n - h) & mask];
-        const float s = scale * __ldg(&P.prescale[n]);
-        dst[n] = make_float2(s * v.x, s * v.y);
-      }
-    }
+    const float scale = (valid && !ZF && rg.mirror) ? 0.5f : 1.0f;
+    float2* dst = const_cast<float2*>(P.pt) + (size_t)(valid ? row : 0) * nt;
+    fft_inverse_crop(X, M, P.mshift, nt, lane, tpr, L.tw, L.Mmax >> P.mshift, dst, P.prescale, scale, valid);
   }
 }
 
