@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -626,11 +627,25 @@ def main():
         nbytes_alg += rows * g["nt"] * 8 + nl * (g["nz"] // 2 + 1) * 8
     peak, peak_src = hbm_peak()
     achieved = nbytes_alg / (st[1] * 1e-3) / 1e9
+    # ALU view of the same launch: 5 M log2 M flops per row FFT; per +-nu pair task
+    # 16 H (tap accumulation) + 40 H (two degree-9 tap polynomials in z^2 and the
+    # two weights per tap pair) + 40 (node position, phase, weight) flops
+    H = max(info["taps"] // 2, 1)
+    flops = 0
+    for g in geoms:
+        half = (g["ny"] if g["dim"] == 3 else g["nx"]) // 2 + 1
+        rows = (g["nx"] if g["dim"] == 3 else 1) * half
+        M = info["M"] if len(geoms) == 1 else 1 << math.ceil(math.log2(max(32, 2 * g["nt"])))
+        flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (56 * H + 40))
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     roofline = {"bound": "hbm", "kernel": "row_forward (prescale + oversampled FFT + KB gather + weight)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(args.config), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": nbytes_alg, "kernel_ms": st[1],
-                "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]}}
+                "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]},
+                "alu_view": {"flops_per_launch": flops, "achieved_tflops": flops / (st[1] * 1e-3) / 1e12,
+                             "peak_tflops": fp32_peak, "frac": flops / (st[1] * 1e-3) / 1e12 / fp32_peak,
+                             "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"}}
     if st_adj is not None:
         roofline["adjoint_stage_ms"] = {"image_fft": st_adj[0], "row_adjoint_kernel": st_adj[1],
                                         "lateral_inverse_fft": st_adj[2]}

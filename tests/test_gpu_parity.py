@@ -291,3 +291,33 @@ def test_3d_power_of_two_both_pipelines(pai, pipeline, shape):
     f, plan = _recon(pai, g, p, K=3)
     assert plan.info["library_ffts"] == (3 if pipeline == "library_ffts" else 0)
     assert rel(f, _ref(g, p)) < TOL
+
+
+def test_stage_errors(pai):
+    """FP32 against FP64 stage by stage: the weighted spectrum (lateral FFT,
+    prescale, oversampled FFT, gather, weight) and the whole reconstruction
+    (plus the inverse FFT), relative L2 against the oracle on the same FP32
+    input.  The table is printed, and written to the file named by
+    PAI_STAGE_ERR_OUT when that is set."""
+    import json
+    import os
+    cases = [("2-D 128x256->128^2, K=3", ph.Geometry(dim=2, nx=128, nt=256, nz=128), 3.0),
+             ("2-D 512x1024->512^2, K=4", ph.Geometry(dim=2, nx=512, nt=1024, nz=512), 4.0),
+             ("3-D 32^2x64->32^3, K=3", ph.Geometry(dim=3, nx=32, ny=32, nt=64, nz=32), 3.0)]
+    rows = []
+    for name, g, K in cases:
+        p = np.asarray(ph.random_data(26, g), np.float32)
+        p64 = p.astype(np.float64)
+        plan = pai.Plan(gdict(g, K=K))
+        S = plan.spectrum(to_gpu(p)).cpu().numpy()
+        F = oracle.spectrum(g, p64)
+        e_spec = rel(S, oracle_half_spectrum(g, F))
+        f = to_np(plan.reconstruct(to_gpu(p)))
+        e_full = rel(f, oracle.image_from_spectrum(g, F))
+        rows.append({"case": name, "spectrum_rel_l2": e_spec, "reconstruction_rel_l2": e_full,
+                     "predicted_window_error": plan.info["predicted_error"]})
+        assert e_spec < TOL and e_full < TOL
+    print(json.dumps(rows, indent=1))
+    if os.environ.get("PAI_STAGE_ERR_OUT"):
+        with open(os.environ["PAI_STAGE_ERR_OUT"], "w") as fh:
+            json.dump(rows, fh, indent=1)
