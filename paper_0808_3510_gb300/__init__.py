@@ -24,7 +24,7 @@ from typing import Iterable, List, Optional, Sequence
 import torch
 
 __all__ = ["Plan", "ForwardModel", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "library_path", "load_library",
-           "geometry", "window_probe", "cutoff_table"]
+           "geometry", "window_probe", "cutoff_table", "cached_plan", "reconstruct", "adjoint"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libpai.so")
@@ -514,3 +514,45 @@ class PAIRecon(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_f: torch.Tensor):
         return ctx.plan.adjoint(grad_f.contiguous()), None
+
+
+# ---------------------------------------------------------------------------
+# functional interface: cached plans per geometry and device
+# ---------------------------------------------------------------------------
+
+_PLAN_CACHE_SIZE = 8
+_plan_cache: "dict" = {}
+_plan_cache_lock = threading.Lock()
+
+
+def _geometry_key(gg: Geometry):
+    return tuple(getattr(gg, name) for name, _ in Geometry._fields_)
+
+
+def cached_plan(g) -> Plan:
+    """A single-problem :class:`Plan` for geometry ``g`` on the current device,
+    created on first use and kept (least recently used first out, at most
+    eight)."""
+    gg = geometry(g)
+    key = (_geometry_key(gg), torch.cuda.current_device())
+    with _plan_cache_lock:
+        plan = _plan_cache.pop(key, None)
+        if plan is None:
+            plan = Plan(gg)
+        _plan_cache[key] = plan
+        while len(_plan_cache) > _PLAN_CACHE_SIZE:
+            _plan_cache.pop(next(iter(_plan_cache))).close()
+    return plan
+
+
+def reconstruct(p: torch.Tensor, g) -> torch.Tensor:
+    """Image [nx][ny][nz] from detector data ``p`` [nx][ny][nt] (Algorithm 2),
+    differentiable in ``p`` (the backward pass is the exact adjoint).  ``g`` is
+    a geometry dict or :class:`Geometry`; its plan is cached."""
+    return PAIRecon.apply(p, cached_plan(g))
+
+
+def adjoint(h: torch.Tensor, g) -> torch.Tensor:
+    """The exact transpose of :func:`reconstruct`: data-shaped output from an
+    image-shaped ``h``."""
+    return cached_plan(g).adjoint(h.contiguous())

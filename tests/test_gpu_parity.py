@@ -321,3 +321,19 @@ def test_stage_errors(pai):
     if os.environ.get("PAI_STAGE_ERR_OUT"):
         with open(os.environ["PAI_STAGE_ERR_OUT"], "w") as fh:
             json.dump(rows, fh, indent=1)
+
+
+def test_functional_interface(pai):
+    """pai.reconstruct / pai.adjoint: cached plans, the same values as an explicit
+    plan, differentiable in the data."""
+    import torch
+    g = ph.Geometry(dim=2, nx=64, nt=128, nz=64, dz=0.9)
+    p = to_gpu(ph.random_data(27, g)).requires_grad_(True)
+    f = pai.reconstruct(p, gdict(g))
+    assert pai.cached_plan(gdict(g)) is pai.cached_plan(gdict(g))
+    ref = pai.Plan(gdict(g)).reconstruct(p.detach())
+    assert torch.equal(f.detach(), ref)
+    h = torch.randn_like(f)
+    (f * h).sum().backward()
+    assert torch.equal(p.grad, pai.adjoint(h, gdict(g)))
+    assert rel(to_np(f.detach()), oracle.reconstruct(g, to_np(p.detach()))) < TOL
