@@ -159,3 +159,38 @@ def test_cutoff_validation(pai):
     with pytest.raises(pai.PAIError) as e:
         batch.set_cutoff(4.0)
     assert e.value.status == 2
+
+
+def test_limited_view_study(pai):
+    """Partial data of growing cutoff width (Sec. 2, Eq. data-part): 2-D, 256
+    detectors x 512 samples -> 256^2, f_circ discs.  The deviation of
+    f_dagger = R (w_cut Q f) from the full-data reconstruction R Q f grows with
+    eps, and every f_dagger matches the oracle's chain on the same data.  The
+    table is printed, and written to the file named by PAI_LIMITED_VIEW_OUT
+    when that is set."""
+    import json
+    import os
+    g = ph.Geometry(dim=2, nx=256, nt=512, nz=256)
+    rng = np.random.default_rng(54)
+    img = ph.fcirc_2d_image(g, ph.random_discs(rng, g, 8, 4.0, 20.0)).astype(np.float32)
+    model = pai.ForwardModel(gdict(g, K=3))
+    plan = pai.Plan(gdict(g, K=3))
+    q = model(to_gpu(img))
+    full = to_np(plan.reconstruct(q))
+    rows = []
+    for eps in (1.0, 16.0, 64.0, 256.0):
+        plan.set_cutoff(eps)
+        gcut = plan.cutoff(q)
+        f_dag = to_np(plan.reconstruct(gcut))
+        data_ref = to_np(q) * oc.weights((g.nx, g.nt), eps)
+        f_ref = oracle.reconstruct(g, to_np(gcut))
+        assert rel(to_np(gcut), data_ref) < 1e-6
+        assert rel(f_dag, f_ref) < TOL
+        rows.append({"eps": eps, "support_radius_steps": float(np.sqrt(eps)),
+                     "rel_l2_vs_full_data": rel(f_dag, full), "rel_l2_vs_image": rel(f_dag, img)})
+    print(json.dumps(rows, indent=1))
+    if os.environ.get("PAI_LIMITED_VIEW_OUT"):
+        with open(os.environ["PAI_LIMITED_VIEW_OUT"], "w") as fh:
+            json.dump(rows, fh, indent=1)
+    dev = [r["rel_l2_vs_full_data"] for r in rows]
+    assert all(a < b for a, b in zip(dev, dev[1:])), dev
