@@ -628,15 +628,16 @@ def main():
     peak, peak_src = hbm_peak()
     achieved = nbytes_alg / (st[1] * 1e-3) / 1e9
     # ALU view of the same launch: 5 M log2 M flops per row FFT; per +-nu pair task
-    # 16 H (tap accumulation) + 40 H (two degree-9 tap polynomials in z^2 and the
-    # two weights per tap pair) + 40 (node position, phase, weight) flops
+    # 16 H (tap accumulation: two nodes x 2H taps x 2 FMA) + 20 H (per tap pair two
+    # 5-term polynomials in z^2 and the two weights) + 40 (node position, phase,
+    # weight) flops
     H = max(info["taps"] // 2, 1)
     flops = 0
     for g in geoms:
         half = (g["ny"] if g["dim"] == 3 else g["nx"]) // 2 + 1
         rows = (g["nx"] if g["dim"] == 3 else 1) * half
         M = info["M"] if len(geoms) == 1 else 1 << math.ceil(math.log2(max(32, 2 * g["nt"])))
-        flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (56 * H + 40))
+        flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (36 * H + 40))
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     roofline = {"bound": "hbm", "kernel": "row_forward (prescale + oversampled FFT + KB gather + weight)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
