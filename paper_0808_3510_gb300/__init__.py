@@ -532,7 +532,7 @@ def _geometry_key(gg: Geometry):
 def cached_plan(g) -> Plan:
     """A single-problem :class:`Plan` for geometry ``g`` on the current device,
     created on first use and kept (least recently used first out, at most
-    eight)."""
+    eight; a dropped plan is destroyed when its last user lets go of it)."""
     gg = geometry(g)
     key = (_geometry_key(gg), torch.cuda.current_device())
     with _plan_cache_lock:
@@ -541,7 +541,8 @@ def cached_plan(g) -> Plan:
             plan = Plan(gg)
         _plan_cache[key] = plan
         while len(_plan_cache) > _PLAN_CACHE_SIZE:
-            _plan_cache.pop(next(iter(_plan_cache))).close()
+            # dropped, not closed: an autograd graph may still hold it for its backward
+            _plan_cache.pop(next(iter(_plan_cache)))
     return plan
 
 
