@@ -337,3 +337,36 @@ def test_functional_interface(pai):
     (f * h).sum().backward()
     assert torch.equal(p.grad, pai.adjoint(h, gdict(g)))
     assert rel(to_np(f.detach()), oracle.reconstruct(g, to_np(p.detach()))) < TOL
+
+
+def _random_geometry(seed):
+    """A seeded random problem: either dimension, even grid sizes (the ABI's
+    rule), spacings and sound speed in [0.5, 2], K in {3, 4}."""
+    rng = np.random.default_rng(1000 + seed)
+    dim = int(rng.integers(2, 4))
+    even = lambda lo, hi: 2 * int(rng.integers(lo // 2, hi // 2 + 1))  # noqa: E731
+    if dim == 2:
+        nx, ny = even(2, 96), 1
+    else:
+        nx, ny = even(2, 24), even(2, 24)
+    g = ph.Geometry(dim=dim, nx=nx, ny=ny, nt=even(2, 300), nz=even(2, 160),
+                    dx=float(rng.uniform(0.5, 2)), dy=float(rng.uniform(0.5, 2)), dt=float(rng.uniform(0.5, 2)),
+                    c=float(rng.uniform(0.5, 2)), dz=float(rng.uniform(0.5, 2)))
+    return g, float(rng.choice([3.0, 4.0]))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_geometries(pai, seed):
+    """Seeded random geometries: the reconstruction against the oracle and the
+    adjoint by the dot-product identity."""
+    from gpu_common import DOT_TOL
+    g, K = _random_geometry(seed)
+    plan = pai.Plan(gdict(g, K=K))
+    p = np.asarray(ph.random_data(60 + seed, g), np.float32)
+    h = np.asarray(ph.random_image(90 + seed, g), np.float32)
+    f = to_np(plan.reconstruct(to_gpu(p)))
+    assert rel(f, oracle.reconstruct(g, p.astype(np.float64))) < TOL, (g, K)
+    a = to_np(plan.adjoint(to_gpu(h)))
+    lhs = float(np.vdot(f, h.astype(np.float64)))
+    rhs = float(np.vdot(p.astype(np.float64), a))
+    assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(f) * np.linalg.norm(h), (g, K)
