@@ -370,3 +370,27 @@ def test_random_geometries(pai, seed):
     lhs = float(np.vdot(f, h.astype(np.float64)))
     rhs = float(np.vdot(p.astype(np.float64), a))
     assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(f) * np.linalg.norm(h), (g, K)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_batches(pai, seed):
+    """Seeded batches of six random problems (mixed dimensions and sizes, one K
+    per batch): every problem of the concatenated output against the oracle,
+    and the batched adjoint by the dot-product identity."""
+    from gpu_common import DOT_TOL
+    geoms = [_random_geometry(100 + 6 * seed + i)[0] for i in range(6)]
+    K = 3.0 if seed % 2 == 0 else 4.0
+    plan = pai.Plan([gdict(g, K=K) for g in geoms])
+    ps = [np.asarray(ph.random_data(200 + i, g), np.float32) for i, g in enumerate(geoms)]
+    hs = [np.asarray(ph.random_image(300 + i, g), np.float32) for i, g in enumerate(geoms)]
+    out = to_np(plan.reconstruct(to_gpu(np.concatenate([p.ravel() for p in ps]))))
+    adj = to_np(plan.adjoint(to_gpu(np.concatenate([h.ravel() for h in hs]))))
+    off = 0
+    for g, p in zip(geoms, ps):
+        n = g.nx * g.ny * g.nz
+        assert rel(out[off: off + n].reshape(g.image_shape), oracle.reconstruct(g, p.astype(np.float64))) < TOL, g
+        off += n
+    h_all = np.concatenate([h.ravel() for h in hs]).astype(np.float64)
+    p_all = np.concatenate([p.ravel() for p in ps]).astype(np.float64)
+    lhs, rhs = float(np.vdot(out, h_all)), float(np.vdot(p_all, adj))
+    assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(out) * np.linalg.norm(h_all)
