@@ -215,3 +215,22 @@ def test_fig5_time_versus_error(pai):
         assert all(a > b for a, b in zip(errs, errs[1:])), (m, errs)
     kb = [by[("kb", c)] for c in (2, 4, 8, 16, 32)]
     assert max(kb) < TOL and max(kb) < by[("linear", 32)], kb
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_methods_random_geometries(pai, seed):
+    """Seeded random geometries (either dimension, spacings and sound speed in
+    [0.5, 2]) for each compared method, against the oracle of the same method."""
+    rng = np.random.default_rng(500 + seed)
+    dim = int(rng.integers(2, 4))
+    even = lambda lo, hi: 2 * int(rng.integers(lo // 2, hi // 2 + 1))  # noqa: E731
+    nx, ny = (even(2, 80), 1) if dim == 2 else (even(2, 20), even(2, 20))
+    g = ph.Geometry(dim=dim, nx=nx, ny=ny, nt=even(4, 260), nz=even(2, 140), dx=float(rng.uniform(0.5, 2)),
+                    dy=float(rng.uniform(0.5, 2)), dt=float(rng.uniform(0.5, 2)), c=float(rng.uniform(0.5, 2)),
+                    dz=float(rng.uniform(0.5, 2)))
+    method, c = METHOD_CASES[seed % len(METHOD_CASES)]
+    if method == "nearest" and om.half_pixel_margin(g, _padded(c, g.nt) / g.nt) <= 1e-6:
+        pytest.skip("a node within 1e-6 of a half-way point")
+    p = ph.random_data(510 + seed, g)
+    f, ref, _ = _run(pai, g, p, method, c)
+    assert rel(f, ref) < TOL, (g, method, c)
