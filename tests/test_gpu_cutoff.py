@@ -194,3 +194,21 @@ def test_limited_view_study(pai):
             json.dump(rows, fh, indent=1)
     dev = [r["rel_l2_vs_full_data"] for r in rows]
     assert all(a < b for a, b in zip(dev, dev[1:])), dev
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cutoff_random_grids(pai, seed):
+    """Seeded random data grids and eps (every axis at least 2 ceil(sqrt(eps)))."""
+    import math
+    rng = np.random.default_rng(800 + seed)
+    eps = float(rng.uniform(1.0, 40.0))
+    R = math.ceil(math.sqrt(eps) - 1e-12)
+    dim = int(rng.integers(2, 4))
+    even = lambda lo, hi: 2 * int(rng.integers(lo // 2, hi // 2 + 1))  # noqa: E731
+    lo = 2 * R + (2 * R) % 2
+    nx, ny = (even(lo, 60), 1) if dim == 2 else (even(lo, 24), even(lo, 24))
+    g = ph.Geometry(dim=dim, nx=nx, ny=ny, nt=even(lo, 90), nz=8)
+    plan = pai.Plan(gdict(g))
+    plan.set_cutoff(eps)
+    p = ph.random_data(810 + seed, g).astype(np.float32)
+    _check_elementwise(to_np(plan.cutoff(to_gpu(p))), oc.apply(p.astype(np.float64), eps))

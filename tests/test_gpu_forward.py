@@ -58,3 +58,20 @@ def test_forward_plan_rejects_other_calls(pai):
     assert lib.pai_adjoint(model._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr())) == 1
     with pytest.raises(pai.PAIError):
         pai.ForwardModel(gdict(g, method="linear"))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_forward_model_random_geometries(pai, seed):
+    """Seeded random geometries (boxes kept at most 128 per axis) against the oracle."""
+    rng = np.random.default_rng(700 + seed)
+    dim = int(rng.integers(2, 4))
+    even = lambda lo, hi: 2 * int(rng.integers(lo // 2, hi // 2 + 1))  # noqa: E731
+    nx, ny = (even(2, 48), 1) if dim == 2 else (even(2, 16), even(2, 16))
+    dx, dz, dt = (float(rng.uniform(0.8, 1.5)) for _ in range(3))
+    c = float(rng.uniform(0.5, 1.0))
+    g = ph.Geometry(dim=dim, nx=nx, ny=ny, nt=even(2, 48), nz=even(2, 40), dx=dx, dy=dx, dt=dt, c=c, dz=dz)
+    model = pai.ForwardModel(gdict(g, K=3))
+    assert max(model.box) <= 128, model.box
+    img = ph.random_image(710 + seed, g).astype(np.float32)
+    got = to_np(model(to_gpu(img)))
+    assert rel(got, oracle.forward_model(g, img.astype(np.float64))) < TOL, g
