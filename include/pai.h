@@ -202,6 +202,20 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
 /* Change the stream later calls are enqueued on (cudaStream_t or NULL).     */
 pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream);
 
+/* Spread of pai_adjoint and pai_forward_model (the transpose of the window
+ * gather, Algorithm 1 read backwards).  Two spreads exist: shared-memory
+ * atomic adds (every node adds its 2H tap contributions to the oversampled
+ * grid at once; the order of the additions into one grid cell, hence the last
+ * bits of the result, may differ from call to call) and tap phases (nodes add
+ * tap by tap in a fixed order, one barrier per phase; bit-identical on
+ * repeated calls).  pai_plan times both and keeps the faster (the
+ * environment variable PAI_SPREAD=atomic or =tap forces one).
+ * deterministic = 1: use the tap phases; deterministic = 0: back to the
+ * plan's choice.  pai_reconstruct is deterministic either way.  Waits for the
+ * plan's stream and drops the plan's captured CUDA graphs (they are captured
+ * again on next use).  Any other value: PAI_ERR_INVALID_ARG.               */
+pai_status pai_set_deterministic(pai_plan_t plan, int deterministic);
+
 /* Fill *info with the plan's parameters.                                     */
 pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info);
 

@@ -126,6 +126,8 @@ def load_library() -> ctypes.CDLL:
         lib.pai_forward_box.restype = st
         lib.pai_profile_stages.argtypes = [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.pai_profile_stages.restype = st
+        lib.pai_set_deterministic.argtypes = [vp, ctypes.c_int]
+        lib.pai_set_deterministic.restype = st
         lib.pai_set_stream.argtypes = [vp, vp]
         lib.pai_set_stream.restype = st
         lib.pai_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -284,6 +286,8 @@ class Plan:
                    "pai_plan_batched")
         self._h = h
         self._lib = lib
+        if torch.are_deterministic_algorithms_enabled():
+            self.set_deterministic(True)
         self.data_numel = sum(_numel(g, g.nt) for g in gs)
         self.image_numel = sum(_numel(g, g.nz) for g in gs)
         self.spectrum_numel = sum(_numel(g, g.nz // 2 + 1) for g in gs)
@@ -382,6 +386,12 @@ class Plan:
                                             int(reps), 1 if adjoint else 0, ms), "pai_profile_stages")
         return [ms[0], ms[1], ms[2]]
 
+    def set_deterministic(self, on: bool = True):
+        """Bit-identical adjoints on repeated calls (tap-phased spread) instead of the
+        faster shared-memory atomic spread (``pai_set_deterministic``).  Plans made
+        while ``torch.use_deterministic_algorithms(True)`` is on start deterministic."""
+        _check(self._lib.pai_set_deterministic(self._h, 1 if on else 0), "pai_set_deterministic")
+
     def set_cutoff(self, eps: float):
         """Attach the data cutoff w_cut with parameter eps (squared sampling steps; 0 removes it)."""
         _check(self._lib.pai_set_cutoff(self._h, float(eps)), "pai_set_cutoff")
@@ -439,6 +449,12 @@ class ForwardModel:
         self.box = tuple(v.value for v in b)
         if cutoff:
             self.set_cutoff(cutoff)
+        if torch.are_deterministic_algorithms_enabled():
+            self.set_deterministic(True)
+
+    def set_deterministic(self, on: bool = True):
+        """Bit-identical results on repeated calls (``pai_set_deterministic``)."""
+        _check(self._lib.pai_set_deterministic(self._h, 1 if on else 0), "pai_set_deterministic")
 
     def set_cutoff(self, eps: float):
         """Return w_cut * (Q f) from now on (the data model of partial data); 0 removes the cutoff."""

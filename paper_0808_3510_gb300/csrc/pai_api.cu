@@ -64,6 +64,8 @@ struct pai_plan_s {
   int TW = 0;  // twiddle table length (power of two >= every FFT length the plan runs)
   int chunk = 128, bin_offset = 0, bin_slot = 0;  // adjoint sorted-bin spread
   int method = PAI_METHOD_KB;                       // PAI_METHOD_*, shared by the batch
+  int spread_mode = 1;                              // adjoint spread (RowLaunch::spread_mode): atomics
+  int spread_tuned = 1;                             // the faster spread found when the plan was built
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
   bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
@@ -275,6 +277,7 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.chunk = P->chunk;
   L.bin_offset = P->bin_offset;
   L.bin_slot = P->bin_slot;
+  L.spread_mode = P->spread_mode;
   return L;
 }
 
@@ -843,6 +846,35 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     for (int T = threads_adj; T >= std::max(tpr_max, 32) && st != PAI_OK; T /= 2) st = finish_shape_adj(T);
     if (st != PAI_OK) return st;
   }
+  // ---- tuner: the adjoint's spread, shared-memory atomics or tap phases ------
+  // (atomics skip the barriers but serialise where many nodes share a cell)
+  const char* env_spread = std::getenv("PAI_SPREAD");
+  if (env_spread && (std::strcmp(env_spread, "atomic") == 0 || std::strcmp(env_spread, "tap") == 0)) {
+    P->spread_tuned = std::strcmp(env_spread, "atomic") == 0 ? 1 : 0;
+  } else if (tune || qmode) {
+    cudaEvent_t e0, e1;
+    PAI_CUDA(cudaEventCreate(&e0));
+    PAI_CUDA(cudaEventCreate(&e1));
+    PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
+    float best_ms[2] = {1e30f, 1e30f};
+    for (int mode = 0; mode < 2; ++mode) {
+      P->spread_mode = mode;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, P->cap_stream);
+        if (enqueue_row(P, true, P->cap_stream, P->threads_adj, P->ctas_adj, P->smem_adj, P->zf_adj) != PAI_OK) break;
+        cudaEventRecord(e1, P->cap_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best_ms[mode] = std::min(best_ms[mode], ms);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    P->spread_tuned = best_ms[1] <= best_ms[0] ? 1 : 0;
+  }
+  P->spread_mode = P->spread_tuned;
   // ---- tuner: when both pipelines apply, keep the faster one ----------------
   // (library kernels for every stage vs cuFFT for the inverse and the adjoint's
   // image-side and data-side transforms), timed on one eager forward pass each
@@ -1118,6 +1150,25 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
   for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
   if (st == PAI_OK)
     for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+  if (prev != plan->device) cudaSetDevice(prev);
+  return st;
+}
+
+pai_status pai_set_deterministic(pai_plan_t plan, int deterministic) {
+  if (!plan || (deterministic != 0 && deterministic != 1)) return PAI_ERR_INVALID_ARG;
+  const int mode = deterministic ? 0 : plan->spread_tuned;
+  if (mode == plan->spread_mode) return PAI_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  pai_status st = cuda_status(cudaStreamSynchronize(plan->stream));
+  if (st == PAI_OK) {
+    // captured graphs hold the launch parameters: capture again on next use
+    for (auto& ge : plan->graphs)
+      if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    plan->graphs.clear();
+    plan->spread_mode = mode;
+  }
   if (prev != plan->device) cudaSetDevice(prev);
   return st;
 }

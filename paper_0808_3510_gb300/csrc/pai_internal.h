@@ -74,6 +74,7 @@ struct RowLaunch {
   int chunk;                   // nodes per bin chunk
   int bin_offset;              // bytes from the start of dynamic shared memory to the bins
   int bin_slot;                // bytes of bins per row slot: chunk * (2H+1) complex, 16-aligned
+  int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)

@@ -972,9 +972,10 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
       }
     }
     __syncthreads();
-    // phase 2: sorted-bin spread (the transpose of the gather).  Node k adds
-    // w_t(fr_k) Q_k to grid cell j0_k + t - H + 1 (mod M), t = 0..2H-1.
-    // Nodes are taken in chunks of at most one node per thread that never mix
+    // phase 2: the spread (the transpose of the gather).  Node k adds
+    // w_t(fr_k) Q_k to grid cell j0_k + t - H + 1 (mod M), t = 0..2H-1, by one
+    // of two schemes (the plan times both and keeps the faster; the tap phases
+    // are also the deterministic choice).  Tap phases: nodes are taken in chunks of at most one node per thread that never mix
     // the two signs (-nu and +nu lists).  Nodes with equal j0 form a run (the
     // list is sorted); for each tap t in turn the head of every run evaluates
     // the tap weight of each of its nodes (tap index uniform over the CTA, so
@@ -985,7 +986,42 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     // M - 2H cells, so in one tap phase no two heads write the same cell; a
     // barrier separates the tap phases.  Every cell receives its terms in a
     // fixed order (chunk, tap, node): deterministic, no atomics.
-    {
+    if (L.spread_mode == 1) {
+      // shared-memory atomics: every node adds its 2H taps straight into the
+      // grid, no tap phases (summation order, hence the last bits, may vary
+      // from run to run)
+      const bool interp = H == 2 && P.method >= PAI_METHOD_LINEAR;
+      for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
+      __syncthreads();
+      for (int i = lane; i < nn; i += tpr) {
+        const float4 nd = N[i];
+        const int j0 = __float_as_int(nd.x);
+        const float z = nd.y - 0.5f, z2 = z * z;
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+          float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+          for (int e = kHalfCoef - 2; e >= 0; --e) {
+            E = fmaf(E, z2, W.ce[p][e]);
+            O = fmaf(O, z2, W.co[p][e]);
+          }
+          float wl = fmaf(z, O, E), wh = fmaf(-z, O, E);
+          if constexpr (H == 2) {
+            if (interp) {
+              wl = interp_tap_weight(P.method, p, nd.y);
+              wh = interp_tap_weight(P.method, 2 * H - 1 - p, nd.y);
+            }
+          }
+          float2* cl = X + PADI((j0 + p - H + 1) & mask);
+          float2* ch = X + PADI((j0 + H - p) & mask);
+          atomicAdd(&cl->x, wl * nd.z);
+          atomicAdd(&cl->y, wl * nd.w);
+          atomicAdd(&ch->x, wh * nd.z);
+          atomicAdd(&ch->y, wh * nd.w);
+        }
+      }
+      __syncthreads();  // every node's taps are in the grid
+    } else {
       const int CH = L.chunk;  // <= tpr
       const bool interp = H == 2 && P.method >= PAI_METHOD_LINEAR;
       for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);

@@ -173,4 +173,5 @@ def test_cutoff_host_validation(pai):
     buf9 = (ctypes.c_double * 9)()
     assert lib.pai_cutoff_table(2, 4.0, buf9, 9, ctypes.byref(R)) == 0 and buf9[8] == 1.0 and abs(buf9[0] - 0.25) < 1e-11
     assert lib.pai_set_cutoff(None, 4.0) == 1
+    assert lib.pai_set_deterministic(None, 1) == 1
     assert lib.pai_cutoff(None, None, None) == 1

@@ -103,10 +103,12 @@ def test_data_model_against_oracle(pai, g, eps):
     import torch
     img = ph.random_image(91, g).astype(np.float32)
     model = pai.ForwardModel(gdict(g, K=3), cutoff=eps)
+    model.set_deterministic(True)
     got = model(to_gpu(img))
     ref = oracle.forward_model(g, img.astype(np.float64)) * oc.weights(g.data_shape, eps)
     assert rel(to_np(got), ref) < TOL
     plain = pai.ForwardModel(gdict(g, K=3))
+    plain.set_deterministic(True)
     q = plain(to_gpu(img))
     plain.set_cutoff(eps)
     assert torch.equal(plain.cutoff(q), got)

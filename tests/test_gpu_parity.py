@@ -328,6 +328,7 @@ def test_functional_interface(pai):
     plan, differentiable in the data."""
     import torch
     g = ph.Geometry(dim=2, nx=64, nt=128, nz=64, dz=0.9)
+    pai.cached_plan(gdict(g)).set_deterministic(True)  # so the two adjoints below agree bit for bit
     p = to_gpu(ph.random_data(27, g)).requires_grad_(True)
     f = pai.reconstruct(p, gdict(g))
     assert pai.cached_plan(gdict(g)) is pai.cached_plan(gdict(g))
@@ -394,3 +395,60 @@ def test_random_batches(pai, seed):
     p_all = np.concatenate([p.ravel() for p in ps]).astype(np.float64)
     lhs, rhs = float(np.vdot(out, h_all)), float(np.vdot(p_all, adj))
     assert abs(lhs - rhs) < DOT_TOL * np.linalg.norm(out) * np.linalg.norm(h_all)
+
+
+@pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+                               ph.Geometry(dim=3, nx=32, ny=24, nt=64, nz=32, dz=0.8)], ids=["2d", "3d"])
+def test_deterministic_spread(pai, g):
+    """pai_set_deterministic: the tap-phased spread repeats bit for bit; the
+    default atomic spread agrees with it to FP32 rounding; plans made under
+    torch.use_deterministic_algorithms(True) start deterministic."""
+    import torch
+    h = to_gpu(ph.random_image(28, g))
+    plan = pai.Plan(gdict(g))
+    fast = plan.adjoint(h).clone()
+    plan.set_deterministic(True)
+    a, b = plan.adjoint(h).clone(), plan.adjoint(h).clone()
+    assert torch.equal(a, b)
+    assert rel(to_np(fast), to_np(a)) < 1e-6
+    plan.set_deterministic(False)
+    assert rel(to_np(plan.adjoint(h)), to_np(a)) < 1e-6
+    model = pai.ForwardModel(gdict(g, K=3))
+    model.set_deterministic(True)
+    f = to_gpu(ph.random_image(29, g))
+    assert torch.equal(model(f).clone(), model(f).clone())
+    prev = torch.are_deterministic_algorithms_enabled()
+    torch.use_deterministic_algorithms(True)
+    try:
+        plan2 = pai.Plan(gdict(g))
+        assert torch.equal(plan2.adjoint(h).clone(), plan2.adjoint(h).clone())
+    finally:
+        torch.use_deterministic_algorithms(prev)
+
+
+@pytest.mark.parametrize("mode", ["atomic", "tap"])
+@pytest.mark.parametrize("g,method", [(ph.Geometry(dim=2, nx=96, nt=200, nz=80, dz=0.9), "kb"),
+                                      (ph.Geometry(dim=3, nx=20, ny=16, nt=48, nz=24, dy=1.2), "kb"),
+                                      (ph.Geometry(dim=2, nx=64, nt=128, nz=64), "linear")],
+                         ids=["2d", "3d", "2d-linear"])
+def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
+    """Both spreads, forced with PAI_SPREAD (the tuner may prefer either), for the
+    adjoint against the oracle's adjoint, and the forward model against its oracle."""
+    import oracle.methods as om
+    monkeypatch.setenv("PAI_SPREAD", mode)
+    plan = pai.Plan(gdict(g, method=method, oversampling=2.0))
+    h = np.asarray(ph.random_image(30, g), np.float32)
+    got = to_np(plan.adjoint(to_gpu(h)))
+    if method == "kb":
+        ref = oracle.adjoint(g, h.astype(np.float64))
+        assert rel(got, ref) < TOL
+    else:
+        p = np.asarray(ph.random_data(31, g), np.float32)
+        Rp = om.reconstruct(g, p.astype(np.float64), method, 2.0).ravel()
+        lhs = float(np.vdot(Rp, h.astype(np.float64).ravel()))
+        rhs = float(np.vdot(p.astype(np.float64).ravel(), got.ravel()))
+        assert abs(lhs - rhs) < 1e-6 * np.linalg.norm(Rp) * np.linalg.norm(h)
+    if method == "kb":
+        model = pai.ForwardModel(gdict(g, K=3))
+        f = np.asarray(ph.random_image(32, g), np.float32)
+        assert rel(to_np(model(to_gpu(f))), oracle.forward_model(g, f.astype(np.float64))) < TOL
