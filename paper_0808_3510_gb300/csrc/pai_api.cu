@@ -849,15 +849,19 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // ---- tuner: the adjoint's spread, shared-memory atomics or tap phases ------
   // (atomics skip the barriers but serialise where many nodes share a cell)
   const char* env_spread = std::getenv("PAI_SPREAD");
-  if (env_spread && (std::strcmp(env_spread, "atomic") == 0 || std::strcmp(env_spread, "tap") == 0)) {
-    P->spread_tuned = std::strcmp(env_spread, "atomic") == 0 ? 1 : 0;
+  const int env_mode = !env_spread ? -1
+                       : std::strcmp(env_spread, "tap") == 0 ? 0
+                       : std::strcmp(env_spread, "atomic") == 0 ? 1
+                       : std::strcmp(env_spread, "runs") == 0 ? 2 : -1;
+  if (env_mode >= 0) {
+    P->spread_tuned = env_mode;
   } else if (tune || qmode) {
     cudaEvent_t e0, e1;
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
-    float best_ms[2] = {1e30f, 1e30f};
-    for (int mode = 0; mode < 2; ++mode) {
+    float best_ms[3] = {1e30f, 1e30f, 1e30f};
+    for (int mode = 0; mode < 3; ++mode) {
       P->spread_mode = mode;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, P->cap_stream);
@@ -872,7 +876,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
-    P->spread_tuned = best_ms[1] <= best_ms[0] ? 1 : 0;
+    P->spread_tuned = 0;
+    for (int mode = 1; mode < 3; ++mode)
+      if (best_ms[mode] < best_ms[P->spread_tuned]) P->spread_tuned = mode;
   }
   P->spread_mode = P->spread_tuned;
   // ---- tuner: when both pipelines apply, keep the faster one ----------------

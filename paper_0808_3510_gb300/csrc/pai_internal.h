@@ -74,7 +74,8 @@ struct RowLaunch {
   int chunk;                   // nodes per bin chunk
   int bin_offset;              // bytes from the start of dynamic shared memory to the bins
   int bin_slot;                // bytes of bins per row slot: chunk * (2H+1) complex, 16-aligned
-  int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics
+  int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics per
+                               // node, 2 shared-memory atomics per run of nodes with equal j0
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)

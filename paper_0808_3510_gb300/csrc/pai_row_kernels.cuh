@@ -974,8 +974,8 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     __syncthreads();
     // phase 2: the spread (the transpose of the gather).  Node k adds
     // w_t(fr_k) Q_k to grid cell j0_k + t - H + 1 (mod M), t = 0..2H-1, by one
-    // of two schemes (the plan times both and keeps the faster; the tap phases
-    // are also the deterministic choice).  Tap phases: nodes are taken in chunks of at most one node per thread that never mix
+    // of three schemes (the plan times them and keeps the fastest; the tap
+    // phases are also the deterministic choice).  Tap phases: nodes are taken in chunks of at most one node per thread that never mix
     // the two signs (-nu and +nu lists).  Nodes with equal j0 form a run (the
     // list is sorted); for each tap t in turn the head of every run evaluates
     // the tap weight of each of its nodes (tap index uniform over the CTA, so
@@ -1021,6 +1021,51 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
         }
       }
       __syncthreads();  // every node's taps are in the grid
+    } else if (L.spread_mode == 2) {
+      // shared-memory atomics per run: the first node of each run of equal j0
+      // sums the run's weighted terms for every tap and adds each sum with one
+      // atomic, so clusters of nodes on few cells cost few atomics
+      const bool interp = H == 2 && P.method >= PAI_METHOD_LINEAR;
+      for (int g = lane; g < M; g += tpr) X[PADI(g)] = make_float2(0.f, 0.f);
+      __syncthreads();
+      for (int i = lane; i < nn; i += tpr) {
+        const int j0 = __float_as_int(N[i].x);
+        if (i > 0 && __float_as_int(N[i - 1].x) == j0) continue;  // not the first node of its run
+        int run = 1;
+        while (i + run < nn && __float_as_int(N[i + run].x) == j0) ++run;
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+          float lx = 0.f, ly = 0.f, hx = 0.f, hy = 0.f;  // taps p and 2H-1-p
+          for (int r = 0; r < run; ++r) {
+            const float4 nd = N[i + r];
+            const float z = nd.y - 0.5f, z2 = z * z;
+            float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+            for (int e = kHalfCoef - 2; e >= 0; --e) {
+              E = fmaf(E, z2, W.ce[p][e]);
+              O = fmaf(O, z2, W.co[p][e]);
+            }
+            float wl = fmaf(z, O, E), wh = fmaf(-z, O, E);
+            if constexpr (H == 2) {
+              if (interp) {
+                wl = interp_tap_weight(P.method, p, nd.y);
+                wh = interp_tap_weight(P.method, 2 * H - 1 - p, nd.y);
+              }
+            }
+            lx = fmaf(wl, nd.z, lx);
+            ly = fmaf(wl, nd.w, ly);
+            hx = fmaf(wh, nd.z, hx);
+            hy = fmaf(wh, nd.w, hy);
+          }
+          float2* cl = X + PADI((j0 + p - H + 1) & mask);
+          float2* ch = X + PADI((j0 + H - p) & mask);
+          atomicAdd(&cl->x, lx);
+          atomicAdd(&cl->y, ly);
+          atomicAdd(&ch->x, hx);
+          atomicAdd(&ch->y, hy);
+        }
+      }
+      __syncthreads();  // every run's taps are in the grid
     } else {
       const int CH = L.chunk;  // <= tpr
       const bool interp = H == 2 && P.method >= PAI_METHOD_LINEAR;

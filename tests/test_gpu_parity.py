@@ -426,7 +426,7 @@ def test_deterministic_spread(pai, g):
         torch.use_deterministic_algorithms(prev)
 
 
-@pytest.mark.parametrize("mode", ["atomic", "tap"])
+@pytest.mark.parametrize("mode", ["atomic", "runs", "tap"])
 @pytest.mark.parametrize("g,method", [(ph.Geometry(dim=2, nx=96, nt=200, nz=80, dz=0.9), "kb"),
                                       (ph.Geometry(dim=3, nx=20, ny=16, nt=48, nz=24, dy=1.2), "kb"),
                                       (ph.Geometry(dim=2, nx=64, nt=128, nz=64), "linear")],
