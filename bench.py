@@ -275,6 +275,84 @@ def aggregate_over_ranks(ms_local: float, voxels_local: int, device=None):
     return ms_max, float(s.item()) / (ms_max * 1e-3)
 
 
+
+def timed_steps(fn, reps, flush, stream):
+    """Mean CUDA-event milliseconds of fn() over reps steps, L2 flushed before each."""
+    import torch
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(float(i & 7))
+        e0[i].record(stream)
+        fn()
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / reps
+
+
+def compare_batched_plain(pai, geoms, p, out, batched_ms, flush, stream, reps=20):
+    """The problems of a batched plan as separate single-problem plans run one
+    after another on the same stream: graph-replayed plans (each plan replays
+    its own captured CUDA graph, as a user's single plan does) and eager plans
+    (no graph).  Returns the batched-vs-plain record of the bench line."""
+    import torch
+    ins, outs, off_i, off_o = [], [], 0, 0
+    sizes = []
+    for g in geoms:
+        gg = pai.geometry(g)
+        ni = gg.nx * (gg.ny if gg.dim == 3 else 1) * gg.nt
+        no = gg.nx * (gg.ny if gg.dim == 3 else 1) * gg.nz
+        sizes.append((ni, no))
+    res = {"batched_ms_per_step": batched_ms, "problems": len(geoms)}
+    for mode in ("graph", "eager"):
+        if mode == "eager":
+            os.environ["PAI_USE_GRAPH"] = "0"
+        try:
+            plans = [pai.Plan(g) for g in geoms]
+        finally:
+            os.environ.pop("PAI_USE_GRAPH", None)
+        ins, outs, off_i, off_o = [], [], 0, 0
+        for pl, (ni, no) in zip(plans, sizes):
+            ins.append(p.view(-1)[off_i: off_i + ni].view(pl._out_shape("nt")))
+            outs.append(out.view(-1)[off_o: off_o + no].view(pl._out_shape("nz")))
+            off_i += ni
+            off_o += no
+
+        def run_all():
+            for pl, a, o in zip(plans, ins, outs):
+                pl.reconstruct(a, o)
+        for _ in range(3):
+            run_all()
+        torch.cuda.synchronize()
+        res[f"plain_{mode}_ms_per_step"] = timed_steps(run_all, reps, flush, stream)
+        for pl in plans:
+            pl.close()
+    res["plain_ms_per_step"] = res["plain_graph_ms_per_step"]
+    res["speedup"] = res["plain_graph_ms_per_step"] / batched_ms
+    res["speedup_vs_plain_eager"] = res["plain_eager_ms_per_step"] / batched_ms
+    res["plain"] = (f"{len(geoms)} separate single-problem plans on the same stream, one after another; "
+                    "'speedup' against graph-replayed plans, 'speedup_vs_plain_eager' against eager plans")
+    return res
+
+
+def fp32_fma_peak(dev, clocks):
+    """FP32 FMA peak in TFLOP/s: SMs (queried) x 128 FP32 lanes per SM (sm_100
+    family) x 2 flops x the maximum SM clock (nvidia-smi, sampled during the
+    timed region; else the measured-peaks file)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, src = None, None
+    if clocks and clocks.get("sm_max_mhz"):
+        mhz, src = float(clocks["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    else:
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+            src = "MEASURED_PEAKS.json sm_max_mhz"
+        except Exception:
+            mhz, src = 2070.0, "nominal 2070 MHz"
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    return peak, f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x {mhz:g} MHz ({src})"
+
 # ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
@@ -497,6 +575,8 @@ def main():
                                                             "datamodel2d", "cutoff2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-problem batched-vs-plain measurement of the default run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -638,7 +718,7 @@ def main():
         rows = (g["nx"] if g["dim"] == 3 else 1) * half
         M = info["M"] if len(geoms) == 1 else 1 << math.ceil(math.log2(max(32, 2 * g["nt"])))
         flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (36 * H + 40))
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_peak, fp32_src = fp32_fma_peak(dev, clocks)
     roofline = {"bound": "hbm", "kernel": "row_forward (prescale + oversampled FFT + KB gather + weight)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(args.config), "peak_source": peak_src,
@@ -646,65 +726,35 @@ def main():
                 "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]},
                 "alu_view": {"flops_per_launch": flops, "achieved_tflops": flops / (st[1] * 1e-3) / 1e12,
                              "peak_tflops": fp32_peak, "frac": flops / (st[1] * 1e-3) / 1e12 / fp32_peak,
-                             "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"}}
+                             "peak_source": fp32_src}}
     if st_adj is not None:
         roofline["adjoint_stage_ms"] = {"image_fft": st_adj[0], "row_adjoint_kernel": st_adj[1],
                                         "lateral_inverse_fft": st_adj[2]}
 
-    # batched vs plain: the same problems as separate plans, one after another, no graph
+    # batched vs plain: the same problems as separate single-problem plans, one
+    # after another (graph-replayed, the fair comparison, and eager)
     batched = None
     if multi:
-        os.environ["PAI_USE_GRAPH"] = "0"
-        plans = [pai.Plan(g) for g in geoms]
-        del os.environ["PAI_USE_GRAPH"]
-        ins, outs, off_i, off_o = [], [], 0, 0
-        for g, pl in zip(geoms, plans):
-            ni, no = pl.data_numel, pl.image_numel
-            ins.append(p[off_i: off_i + ni].view(pl._out_shape("nt")))
-            outs.append(out[off_o: off_o + no].view(pl._out_shape("nz")))
-            off_i += ni
-            off_o += no
+        batched = compare_batched_plain(pai, geoms, p, out, ms, flush, stream)
+    elif args.config == "large2d" and not args.no_batched and rank == 0:
+        # the default run also measures the batched half of the metric on the
+        # 64-problem uneven batch (the headline value stays the single problem)
+        bdesc, bgeoms, bdatas = workload("batched2d", seed=0)
+        bflat = torch.from_numpy(np.concatenate([d.ravel() for d in bdatas]).astype(np.float32)).to(dev)
+        del bdatas
+        bplan = pai.Plan(bgeoms)
+        bout = torch.empty(bplan.image_numel, device=dev, dtype=torch.float32)
         for _ in range(3):
-            for pl, a, o in zip(plans, ins, outs):
-                pl.reconstruct(a, o)
+            bplan.reconstruct(bflat, bout)
         torch.cuda.synchronize()
-        reps = 20
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        for i in range(reps):
-            flush.fill_(float(i & 7))
-            e0.record(stream)
-            for pl, a, o in zip(plans, ins, outs):
-                pl.reconstruct(a, o)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        plain_ms = tot / reps
-        batched = {"batched_ms_per_step": ms, "plain_ms_per_step": plain_ms,
-                   "plain": f"{len(geoms)} separate plans, sequential, eager (no CUDA graph)",
-                   "speedup": plain_ms / ms}
-        for pl in plans:
-            pl.close()
-        if args.config == "frames2d":
-            # the same frames through one graph-replayed single-frame plan each
-            plans = [pai.Plan(g) for g in geoms]
-            for _ in range(3):
-                for pl, a, o in zip(plans, ins, outs):
-                    pl.reconstruct(a, o)
-            torch.cuda.synchronize()
-            tot = 0.0
-            for i in range(reps):
-                flush.fill_(float(i & 7))
-                e0.record(stream)
-                for pl, a, o in zip(plans, ins, outs):
-                    pl.reconstruct(a, o)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            batched["plain_graph_ms_per_step"] = tot / reps
-            batched["speedup_vs_plain_graph"] = (tot / reps) / ms
-            for pl in plans:
-                pl.close()
+        bms = timed_steps(lambda: bplan.reconstruct(bflat, bout), 20, flush, stream)
+        batched = compare_batched_plain(pai, bgeoms, bflat, bout, bms, flush, stream)
+        batched["workload"] = f"batched2d: {bdesc}"
+        batched["voxels_per_step"] = voxels_of(bgeoms)
+        batched["batched_voxels_per_s"] = voxels_of(bgeoms) / (bms * 1e-3)
+        bplan.close()
+        del bflat, bout
+        torch.cuda.empty_cache()
 
     # end to end through host memory: a stream of steps through the pipelined
     # host call (upload, transforms and download of consecutive steps overlap);

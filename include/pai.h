@@ -324,10 +324,9 @@ pai_status pai_cutoff(pai_plan_t plan, const float* d_in, float* d_out);
 /* The fused row stage of pai_spectrum (prescale, oversampled FFT, window
  * gather and weight for every lateral-frequency row) for ONE problem, with no
  * device allocation at all.  The paper has no counterpart: this entry point
- * exists for callers that may not call cudaMalloc / cudaFree (code running
- * inside another framework's stream capture, processes whose device memory is
- * already reserved by another allocator or pool, real-time loops in which an
- * allocation's implicit synchronisation is not allowed).
+ * exists for callers that may not call cudaMalloc / cudaFree (processes whose
+ * device memory is already reserved by another allocator or pool, real-time
+ * loops in which an allocation's implicit synchronisation is not allowed).
  * g:      problem statement, as for pai_plan (host, read during the call).
  * d_pt:   device, interleaved complex64 lateral spectrum rows [rows][nt], the
  *         output of an unnormalised real-to-complex FFT of p over the lateral
@@ -339,11 +338,15 @@ pai_status pai_cutoff(pai_plan_t plan, const float* d_in, float* d_out);
  * Scratch: every table, descriptor and the work counter live in one static
  * device array of PAI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
  * library holds until exit; geometries whose tables exceed it return
- * PAI_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.
- * Each call copies its tables from host memory into the array (this waits for
- * the stream's earlier work) and zeroes the work counter; the array keeps the
- * last call's contents, and calls that overlap on the GPU race on it.
+ * PAI_ERR_UNSUPPORTED, checked on the host before any CUDA call and before the
+ * pointers are looked at.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress).  Each call fills its tables in a host
+ * buffer and copies them into the array with a cudaMemcpyAsync on cuda_stream
+ * (from pageable memory: the driver stages the bytes before the call returns),
+ * zeroing the work counter; the copy is ordered after the stream's earlier
+ * work, so consecutive calls on one stream are safe.  The array keeps the last
+ * call's contents, and calls that overlap on the GPU (other streams, other
+ * threads) race on it.
  * Calls no cudaMalloc, cudaFree or allocating library routine.              */
 pai_status pai_spectrum_rows_noalloc(const pai_geometry* g, const float* d_pt, float* d_fhat, void* cuda_stream);
 

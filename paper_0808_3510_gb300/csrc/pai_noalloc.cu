@@ -3,23 +3,21 @@
 // allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc / cudaFree are off limits --
-// inside another framework's stream capture, in a process whose device memory
-// is already fully reserved by someone else's caching allocator or memory
-// pool, or in a real-time loop where an allocation (which may synchronise the
-// device) is not allowed.  Such a caller passes its own input and output
-// buffers; everything else the kernel needs (its descriptor, work list, work
-// counter, twiddle table and window / node tables) lives in one file-scope
-// static device array of PAI_NOALLOC_SCRATCH_BYTES bytes that every GPU which
-// loads the library holds until the process exits.
+// a process whose device memory is already fully reserved by someone else's
+// caching allocator or memory pool, or a real-time loop where an allocation
+// (which may synchronise the device) is not allowed.  Such a caller passes its
+// own input and output buffers; everything else the kernel needs (its
+// descriptor, work list, work counter, twiddle table and window / node tables)
+// lives in one file-scope static device array of PAI_NOALLOC_SCRATCH_BYTES
+// bytes that every GPU which loads the library holds until the process exits.
 //
 // Host code cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on it.  That first call should therefore come before any
-// stream capture.  All calls share the array and it keeps the previous call's
-// contents: each call rewrites every byte the kernel reads (the work counter
-// included, which must start at zero).  Calls whose work overlaps on the GPU
-// race on the array.
+// first call made on it.  All calls share the array and it keeps the previous
+// call's contents: each call rewrites every byte the kernel reads (the work
+// counter included, which must start at zero) with one stream-ordered copy.
+// Calls whose work overlaps on the GPU race on the array.
 #include <cstring>
 #include <mutex>
 
@@ -48,7 +46,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const float* d_pt, float* d_fhat,
                                                 void* cuda_stream) {
   using namespace pai;
-  if (!g_in || !d_pt || !d_fhat) return PAI_ERR_INVALID_ARG;
+  if (!g_in) return PAI_ERR_INVALID_ARG;
   pai_geometry g = *g_in;
   if (g.dim == 2) {
     g.ny = 1;
@@ -87,6 +85,9 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   const size_t o_zt = off;    off = align256(off + (size_t)(g.nz / 2 + 1) * 4 * sizeof(float));
   const size_t used = off;
   if (used > kScratchBytes) return PAI_ERR_UNSUPPORTED;
+  // the pointers are checked after the size, so an oversized geometry is
+  // rejected on the host whatever the caller passes
+  if (!d_pt || !d_fhat) return PAI_ERR_INVALID_ARG;
 
   WindowPoly poly;
   if (!(fit_window(0, pp.H, pp.beta, &poly) < 1e-6)) return PAI_ERR_UNSUPPORTED;

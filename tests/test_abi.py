@@ -175,3 +175,19 @@ def test_cutoff_host_validation(pai):
     assert lib.pai_set_cutoff(None, 4.0) == 1
     assert lib.pai_set_deterministic(None, 1) == 1
     assert lib.pai_cutoff(None, None, None) == 1
+
+
+def test_noalloc_rejects_oversized_tables_on_the_host(pai):
+    """A geometry whose tables exceed the static scratch array is rejected
+    before any CUDA call; the size is checked before the pointers, so NULL
+    buffers (which would fail the pointer check) prove the rejection came from
+    the size check and nothing was launched."""
+    lib = pai.load_library()
+    # 2-D, 65537 depth-table entries of 16 bytes: just over 1 MiB
+    big = pai.geometry(dict(dim=2, nx=2, nt=64, nz=131072))
+    assert lib.pai_spectrum_rows_noalloc(ctypes.byref(big), None, None, None) == 2
+    g3 = pai.geometry(dict(dim=3, nx=2048, ny=2048, nt=64, nz=64))
+    assert lib.pai_spectrum_rows_noalloc(ctypes.byref(g3), None, None, None) == 2
+    # a geometry that fits reaches the pointer check instead
+    small = pai.geometry(dict(dim=2, nx=16, nt=64, nz=32))
+    assert lib.pai_spectrum_rows_noalloc(ctypes.byref(small), None, None, None) == 1
