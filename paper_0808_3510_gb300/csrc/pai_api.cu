@@ -66,6 +66,11 @@ struct pai_plan_s {
   int method = PAI_METHOD_KB;                       // PAI_METHOD_*, shared by the batch
   int spread_mode = 1;                              // adjoint spread (RowLaunch::spread_mode): atomics
   int spread_tuned = 1;                             // the faster spread found when the plan was built
+  int spread_det = 0;                               // the faster deterministic spread (0 or 3)
+  bool pairs_ok = false;                            // spread mode 3 applies to every problem of the plan
+  int grid2_off = 0;                                // mode 3: complex offset of the second grids (0 = none)
+  size_t smem_adj3 = 0;                             // mode 3: shared memory of the adjoint row kernel
+  int ctas_adj3 = 0;                                //         and its CTA count
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
   bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
@@ -278,12 +283,18 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.bin_offset = P->bin_offset;
   L.bin_slot = P->bin_slot;
   L.spread_mode = P->spread_mode;
+  L.grid2_off = P->grid2_off;
   return L;
 }
 
 pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads, int ctas, size_t smem,
                        bool zf = false) {
   RowLaunch L = make_launch(P, adjoint);
+  if (adjoint && P->spread_mode == 3) {
+    // the pair spread's second grids follow the node lists
+    smem = P->smem_adj3;
+    ctas = P->ctas_adj3;
+  }
   PAI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(int), s));
   cudaError_t e = adjoint ? launch_row_adjoint(L, P->poly, threads, ctas, smem, s, zf)
                           : launch_row_forward(L, P->poly, threads, ctas, smem, s, zf);
@@ -764,10 +775,36 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     if (P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
     const int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);
     if (occ_a < 1) return PAI_ERR_UNSUPPORTED;
+    // spread mode 3 (node pairs into warp-private grids): windowed methods,
+    // rows of one or two warps, and 32 consecutive pairs spanning fewer than
+    // M - 2H cells (consecutive nodes of one sign are at most M c dt / (nz dz)
+    // cells apart)
+    P->pairs_ok = !method_interp(P->method) && std::getenv("PAI_NO_PAIRS") == nullptr;
+    bool two_warps = false;
+    for (auto& p : P->probs) {
+      const double g1 = std::ceil((double)p.M * p.g.c * p.g.dt / (p.g.nz * p.g.dz)) + 1.0;
+      if (p.tpr != 32 && p.tpr != 64) P->pairs_ok = false;
+      if (!(32.0 * g1 + 2.0 * P->H + 2.0 < (double)p.M)) P->pairs_ok = false;
+      two_warps = two_warps || p.tpr == 64;
+    }
+    P->grid2_off = 0;
+    P->smem_adj3 = P->smem_adj;
+    P->ctas_adj3 = 0;
+    if (P->pairs_ok) {
+      if (two_warps) {
+        P->grid2_off = P->bin_offset / (int)sizeof(float2);
+        P->smem_adj3 = (size_t)P->bin_offset + region;
+      }
+      const int occ3 = P->smem_adj3 <= (size_t)smem_optin
+                           ? row_kernel_max_ctas_per_sm(true, T, P->smem_adj3, P->H, P->zf) : 0;
+      if (occ3 < 1) P->pairs_ok = false;
+      P->ctas_adj3 = occ3 * sms;
+    }
     std::vector<WorkItem> items;
     build_items(T, items);
     P->nitems_adj = (int)items.size();
     P->ctas_adj = std::min(P->nitems_adj, occ_a * sms);
+    P->ctas_adj3 = std::min(P->nitems_adj, P->ctas_adj3);
     if (P->d_items_adj == P->d_items_fwd) P->d_items_adj = nullptr;
     cudaFree(P->d_items_adj);
     P->d_items_adj = nullptr;
@@ -849,10 +886,13 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // ---- tuner: the adjoint's spread, shared-memory atomics or tap phases ------
   // (atomics skip the barriers but serialise where many nodes share a cell)
   const char* env_spread = std::getenv("PAI_SPREAD");
-  const int env_mode = !env_spread ? -1
-                       : std::strcmp(env_spread, "tap") == 0 ? 0
-                       : std::strcmp(env_spread, "atomic") == 0 ? 1
-                       : std::strcmp(env_spread, "runs") == 0 ? 2 : -1;
+  int env_mode = !env_spread ? -1
+                 : std::strcmp(env_spread, "tap") == 0 ? 0
+                 : std::strcmp(env_spread, "atomic") == 0 ? 1
+                 : std::strcmp(env_spread, "runs") == 0 ? 2
+                 : std::strcmp(env_spread, "pairs") == 0 ? 3 : -1;
+  if (env_mode == 3 && !P->pairs_ok) env_mode = 0;
+  P->spread_det = P->pairs_ok ? 3 : 0;
   if (env_mode >= 0) {
     P->spread_tuned = env_mode;
   } else if (tune || qmode) {
@@ -860,8 +900,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
-    float best_ms[3] = {1e30f, 1e30f, 1e30f};
-    for (int mode = 0; mode < 3; ++mode) {
+    float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    for (int mode = 0; mode < 4; ++mode) {
+      if (mode == 3 && !P->pairs_ok) continue;
       P->spread_mode = mode;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, P->cap_stream);
@@ -877,8 +918,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     cudaEventDestroy(e1);
     cudaGetLastError();
     P->spread_tuned = 0;
-    for (int mode = 1; mode < 3; ++mode)
+    for (int mode = 1; mode < 4; ++mode)
       if (best_ms[mode] < best_ms[P->spread_tuned]) P->spread_tuned = mode;
+    P->spread_det = (P->pairs_ok && best_ms[3] < best_ms[0]) ? 3 : 0;
   }
   P->spread_mode = P->spread_tuned;
   // ---- tuner: when both pipelines apply, keep the faster one ----------------
@@ -1162,7 +1204,7 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
 
 pai_status pai_set_deterministic(pai_plan_t plan, int deterministic) {
   if (!plan || (deterministic != 0 && deterministic != 1)) return PAI_ERR_INVALID_ARG;
-  const int mode = deterministic ? 0 : plan->spread_tuned;
+  const int mode = deterministic ? (plan->spread_tuned == 3 ? 3 : plan->spread_det) : plan->spread_tuned;
   if (mode == plan->spread_mode) return PAI_OK;
   int prev = 0;
   cudaGetDevice(&prev);

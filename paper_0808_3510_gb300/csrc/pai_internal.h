@@ -14,9 +14,11 @@ namespace pai {
 // Largest half tap count supported by the row kernels: taps per node = 2H <= 24.
 constexpr int kMaxH = 12;
 // Polynomial degree of each tap's window polynomial in z = frac - 1/2.
-// Even part: z^0, z^2, ..., z^8 (5 coefficients); odd part: z^1, ..., z^9.
-constexpr int kDeg = 9;
-constexpr int kHalfCoef = (kDeg + 1) / 2;  // 5
+// Even part: z^0, z^2, ..., z^6 (4 coefficients); odd part: z^1, ..., z^7.
+// Degree 7 fits the Kaiser-Bessel taps as closely as degree 9 does once the
+// FP32 coefficients are rounded (about 3e-8 of the peak for H >= 5 at c = 2).
+constexpr int kDeg = 7;
+constexpr int kHalfCoef = (kDeg + 1) / 2;  // 4
 // Complex values each thread holds during an in-shared-memory FFT pass.
 constexpr int kElemsPerThread = 16;
 
@@ -54,6 +56,7 @@ struct RowProblem {
   int nzshift;             // log2(nz) when nz is a power of two, else 0
   int method;              // PAI_METHOD_*
   int qmode;               // adjoint kernel evaluates the discrete forward model (depth-row layout only)
+  int zslot = 0;           // complex values per row slot of the fused depth transform (nz + nz/32 + 4)
 };
 
 struct WorkItem {
@@ -70,12 +73,17 @@ struct RowLaunch {
   int Mmax;
   int H;                       // half tap count (taps = 2H)
   int fft_region;              // complex values of shared memory used by the row slots (adjoint: nodes follow)
+  int zdepth_off = 0;          // forward depth-row layout: complex offset of the fused depth-transform lines
+                               // (0 = not fused: the kernel writes the depth spectrum F[row][l])
   // adjoint only: sorted-bin spread buffers
   int chunk;                   // nodes per bin chunk
   int bin_offset;              // bytes from the start of dynamic shared memory to the bins
   int bin_slot;                // bytes of bins per row slot: chunk * (2H+1) complex, 16-aligned
   int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics per
-                               // node, 2 shared-memory atomics per run of nodes with equal j0
+                               // node, 2 shared-memory atomics per run of nodes with equal j0, 3 node pairs
+                               // into warp-private grids (deterministic; windowed methods, 32 or 64 threads
+                               // per row)
+  int grid2_off = 0;           // spread mode 3 with two warps per row: complex offset of the second grids
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)

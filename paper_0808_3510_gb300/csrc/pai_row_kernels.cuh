@@ -223,9 +223,11 @@ __device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
 // PADI(a + 16 r) = PADI(a) + 16 r + r/2 (r < 16).  Both hold for every pass
 // after the first radix-16 one (Ns = 16 or a multiple of 256), and for the
 // first pass (Ns = 1) PADI(16 j + r) = PADI(16 j) + r.
-template <int R, bool INV, int OUT>
+// ADD2: the pass reads X + X2 (two padded grids of the same layout summed on
+// load) and writes its outputs to X.
+template <int R, bool INV, int OUT, bool ADD2 = false>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
-                                         int twstride, bool active = true) {
+                                         int twstride, bool active = true, const float2* X2 = nullptr) {
   constexpr int NB = kElemsPerThread / R;
   float2 v[NB][R];
   TwBase<R> t[NB];
@@ -243,6 +245,11 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
         const float2* src = X + PADI(lane + i * tpr);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i][r] = src[r * rs];
+        if (ADD2) {
+          const float2* src2 = X2 + PADI(lane + i * tpr);
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[i][r] = cadd(v[i][r], src2[r * rs]);
+        }
       }
     } else {
 #pragma unroll
@@ -250,6 +257,10 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
         const int j = lane + i * tpr;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i][r] = X[PADI(j + r * MR)];
+        if (ADD2) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[i][r] = cadd(v[i][r], X2[PADI(j + r * MR)]);
+        }
       }
     }
   }
@@ -388,12 +399,21 @@ __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane,
 // kept, and only those 8 outputs are computed: with w = e^{+2 pi i/16},
 // A = inverse DFT8 of the even inputs and B of the odd,
 // Y[t] = A[t] + w^t B[t] (t = 0..3) and Y[t+8] = A[t] - w^t B[t] (t = 4..7).
+// X2 != nullptr: the input is the sum of the grids X and X2 (added as the
+// first pass loads them).
 __device__ __forceinline__ void fft_inverse_crop(float2* X, int M, int mshift, int nt, int lane, int tpr,
                                                  const float2* __restrict__ tw, int twstride, float2* dst,
-                                                 const float* __restrict__ prescale, float scale, bool valid) {
+                                                 const float* __restrict__ prescale, float scale, bool valid,
+                                                 const float2* X2 = nullptr) {
   int Ns = 1;
   const int r0 = mshift & 3;
-  if (r0 == 3) {
+  if (X2) {
+    if (r0 == 3) fft_pass<8, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
+    else if (r0 == 2) fft_pass<4, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
+    else if (r0 == 1) fft_pass<2, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
+    else fft_pass<16, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
+    Ns = r0 == 3 ? 8 : r0 == 2 ? 4 : r0 == 1 ? 2 : 16;
+  } else if (r0 == 3) {
     fft_pass<8, true, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
     Ns = 8;
   } else if (r0 == 2) {
@@ -750,12 +770,15 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
 // for 0 < |l| < nz/2, F[0] = 0 (l = 0 rule), F[-nz/2] = W (P(+|K|) + P(-|K|))/2
 // (Nyquist rule).  One task per |l| evaluates the node pair.  An inverse depth
 // FFT of each line followed by the lateral C2R completes Eq. (fft-1).
-template <int H>
+// PAD: Zs is a shared-memory line in the padded FFT layout (F[l] at
+// Zs[PADI(l)]), the input of the fused depth transform.
+template <int H, bool PAD = false>
 __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPoly& W, const float2* X, float2* Zs,
                                              int row, int lane) {
   const float2 S = P.rowS[row];
   const int nzh = P.nz >> 1;
-  if (lane == 0) Zs[0] = make_float2(0.f, 0.f);
+  auto at = [&](int l) -> float2& { return PAD ? Zs[PADI(l)] : Zs[l]; };
+  if (lane == 0) at(0) = make_float2(0.f, 0.f);
   float4 zt_next = __ldg(&P.zt[min(lane, nzh - 1) + 1]);
   for (int i = lane; i < nzh; i += P.tpr) {
     const int lp = i + 1;
@@ -768,10 +791,10 @@ __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPo
     float2 v, u;
     node_value_pair<H>(P, X, W, j0, fr, v, u);
     if (lp == nzh) {
-      Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
+      at(nzh) = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
     } else {
-      Zs[lp] = make_float2(wt * v.x, wt * v.y);
-      Zs[P.nz - lp] = make_float2(wt * u.x, wt * u.y);
+      at(lp) = make_float2(wt * v.x, wt * v.y);
+      at(P.nz - lp) = make_float2(wt * u.x, wt * u.y);
     }
   }
 }
@@ -805,7 +828,19 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
     fft_first_pass_from_global(X, M, P.nt, lane, tpr, P.pt + (size_t)(valid ? row : 0) * P.nt, P.prescale);
     fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
-    if (valid) {
+    if (ZF && L.zdepth_off > 0) {
+      // fused depth transform: the row's depth spectrum goes to shared memory,
+      // is inverse transformed there (nz / 16 active threads) and the depth
+      // line h[row][z] = sum_l e^{+2 pi i l z / nz} F[l] is written out
+      float2* Fz = smem + L.zdepth_off + slot * P.zslot;
+      if (valid) gather_row_z<H, true>(P, W, X, Fz, row, lane);
+      const int tz = P.nz / kElemsPerThread;
+      fft_smem<true, kLayoutFlat>(Fz, P.nz, P.nzshift, lane, tz, L.tw, L.Mmax >> P.nzshift, lane < tz);
+      if (valid) {
+        float2* h = P.fh + (size_t)row * P.nz;
+        for (int z = lane; z < P.nz; z += tpr) h[z] = Fz[z];
+      }
+    } else if (valid) {
       if (!ZF) gather_row<H>(P, W, X, row, lane);
       else gather_row_z<H>(P, W, X, P.fh + (size_t)row * P.nz, row, lane);
     }
@@ -838,6 +873,185 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
 
+// Adjoint of one row by node pairs and warp-private grids (spread mode 3,
+// windowed methods, row slots of one or two warps).
+//
+// Phase 1: pair i holds the node pair +-x of one depth index (l = i + 1, or
+// j = i in forward-model mode), sorted by x: A[i] = (j0, fr, Q+) for the +x
+// node (x = j0 + fr) and B[i] = Q- for the -x node, each Q the node's input
+// value times the weight and the transpose of its phase, e^{+i pi nu} for +x
+// and its conjugate for -x.  The -x node is taken as (-j0 - 1) + (1 - fr), as
+// the forward gather takes it, so its tap q weighs w_{2H-1-q}(z), z = fr - 1/2:
+// one evaluation of the tap-pair polynomials serves both nodes.
+//
+// Phase 2: warp w of the row slot spreads the pairs [w np / nw, (w+1) np / nw)
+// into its own grid (warp 0: the row slot X, warp 1: X2), so no two warps
+// ever write one grid.  Within a warp 32 consecutive pairs go at a time, one
+// per lane; pairs with equal j0 form a run (the list is sorted), and for each
+// tap pair and each of the four contributions (taps p and 2H-1-p of +x and
+// of -x) the run's terms are summed across its lanes (segmented shuffle sum,
+// only when the 32 pairs hold a run) and the run's first lane adds the sum to
+// its cell with a plain read-modify-write.  Within one such step distinct
+// runs have distinct j0, hence distinct cells (the 32 pairs span fewer than
+// M - 2H cells, checked by the plan); a __syncwarp separates the steps.
+// Every cell therefore receives its terms in a fixed order: the result is
+// bit-repeatable.  The inverse FFT then reads X + X2.
+// Returns whether the row is a mirror row (non-ZF input, both destinations).
+template <int H, bool ZF>
+__device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowPoly& W, int row, bool valid, int lane,
+                                              float2* X, float2* X2, float4* A) {
+  const int tpr = P.tpr, M = P.M, nt = P.nt, mask = M - 1;
+  const int nzh = P.nz >> 1;
+  float2* B = reinterpret_cast<float2*>(A + nzh + 1);
+  bool mirror = true;
+  int np = 0;
+  if (valid) {
+    const float2* Zs = P.fh + (size_t)row * P.nz;  // ZF: the row's depth spectrum Fbar[l mod nz]
+    if (ZF && P.qmode) {
+      // forward model: pair j (j = 0..nz/2) carries c_j / 2 on both nodes,
+      // c_j = F[j] + F[-j] (F[0], F[nz/2] alone); wscale holds 1 / (2 n_lat nz)
+      const float2 S = P.rowS[row];
+      np = nzh + 1;
+      for (int j = lane; j <= nzh; j += tpr) {
+        const float4 zt = __ldg(&P.zt[j]);
+        int j0;
+        float fr, x0;
+        node_position(S, zt, P.B2hi, P.B2lo, j0, fr, x0);
+        float2 y = Zs[j];
+        if (j > 0 && j < nzh) y = cadd(y, Zs[P.nz - j]);
+        const float2 pb = make_float2(P.wscale * y.x, P.wscale * y.y);
+        const float2 ph = node_phase(j0, fr, nt, M, P.nt_over_M);
+        const float2 qp = cmul(pb, ph), qn = cmul(pb, make_float2(ph.x, -ph.y));
+        A[j] = make_float4(__int_as_float(j0), fr, qp.x, qp.y);
+        B[j] = qn;
+      }
+    } else {
+      RowGeom rg;
+      const float2* in1 = nullptr;
+      const float2* in2 = nullptr;
+      if (ZF) {
+        rg.S = P.rowS[row];
+      } else {
+        rg = row_geom(P, row);
+        mirror = rg.mirror;
+        in1 = P.fh + (size_t)rg.d1 * P.lz;
+        in2 = P.fh + (size_t)rg.d2 * P.lz;
+      }
+      np = nzh;
+      for (int i = lane; i < nzh; i += tpr) {
+        const int lp = i + 1;
+        const float4 zt = __ldg(&P.zt[lp]);
+        int j0;
+        float fr, x0;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, x0);
+        const float wt = P.wscale * zt.z / x0;
+        const float2 ph = node_phase(j0, fr, nt, M, P.nt_over_M);
+        const float2 phc = make_float2(ph.x, -ph.y);
+        float2 qp, qn;
+        if (lp == nzh) {
+          // Nyquist: both nodes carry half the l = -nz/2 input
+          float2 y;
+          if (ZF) {
+            y = Zs[nzh];
+          } else {
+            y = in1[lp];
+            if (mirror) {
+              const float2 y2 = in2[lp];
+              y.x += y2.x;
+              y.y -= y2.y;
+            }
+          }
+          const float2 pb = make_float2(0.5f * wt * y.x, 0.5f * wt * y.y);
+          qp = cmul(pb, ph);
+          qn = cmul(pb, phc);
+        } else if (ZF) {
+          const float2 y = Zs[lp], y2 = Zs[P.nz - lp];
+          qp = cmul(make_float2(wt * y.x, wt * y.y), ph);
+          qn = cmul(make_float2(wt * y2.x, wt * y2.y), phc);
+        } else {
+          const float2 y = in1[lp];
+          qp = cmul(make_float2(2.0f * wt * y.x, 2.0f * wt * y.y), ph);
+          if (mirror) {
+            const float2 y2 = in2[lp];
+            qn = cmul(make_float2(2.0f * wt * y2.x, -2.0f * wt * y2.y), phc);
+          } else {
+            qn = make_float2(0.f, 0.f);  // self-conjugate row: no -nu node below the Nyquist entry
+          }
+        }
+        A[i] = make_float4(__int_as_float(j0), fr, qp.x, qp.y);
+        B[i] = qn;
+      }
+    }
+  }
+  __syncthreads();  // pair lists complete (every row slot)
+  const int nw = tpr >> 5;  // warps in the row slot (1 or 2)
+  const int w = lane >> 5, l32 = lane & 31;
+  float2* G = w == 0 ? X : X2;
+  for (int g = l32; g < M; g += 32) G[PADI(g)] = make_float2(0.f, 0.f);
+  __syncwarp();
+  if (valid) {
+    const unsigned full = 0xffffffffu;
+    const int p0 = (np * w) / nw, p1 = (np * (w + 1)) / nw;
+    for (int c0 = p0; c0 < p1; c0 += 32) {
+      const int i = c0 + l32;
+      const bool act = i < p1;
+      const float4 a = act ? A[i] : make_float4(0.f, 0.5f, 0.f, 0.f);
+      const float2 b = act ? B[i] : make_float2(0.f, 0.f);
+      const int j0 = __float_as_int(a.x);
+      const int prev = __shfl_up_sync(full, j0, 1);
+      const bool head = act && (l32 == 0 || prev != j0);
+      const unsigned heads = __ballot_sync(full, head);
+      const unsigned actm = __ballot_sync(full, act);
+      // last lane of this lane's run
+      const unsigned later = heads & (0xfffffffeu << l32);
+      const int last = later ? __ffs(later) - 2 : 31 - __clz(actm);
+      const int span = head ? last - l32 + 1 : 0;
+      const int maxrun = __reduce_max_sync(full, (unsigned)span);
+      const float2 qp = make_float2(a.z, a.w);
+      const float z = a.y - 0.5f, z2 = z * z;
+      const int cp0 = j0 - H + 1;  // cell of tap 0 of +x
+      const int cn0 = -j0 - H;     // cell of tap 0 of -x
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        float E = W.ce[p][kHalfCoef - 1], O = W.co[p][kHalfCoef - 1];
+#pragma unroll
+        for (int e = kHalfCoef - 2; e >= 0; --e) {
+          E = fmaf(E, z2, W.ce[p][e]);
+          O = fmaf(O, z2, W.co[p][e]);
+        }
+        const float wl = fmaf(z, O, E), wh = fmaf(-z, O, E);
+        // taps p and 2H-1-p of +x (weights wl, wh); of -x (wh, wl)
+        float2 c[4] = {mul2(make_float2(wl, wl), qp), mul2(make_float2(wh, wh), qp), mul2(make_float2(wh, wh), b),
+                       mul2(make_float2(wl, wl), b)};
+        if (maxrun > 1) {
+          for (int d = 1; d < maxrun; d <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float tx = __shfl_down_sync(full, c[k].x, d);
+              const float ty = __shfl_down_sync(full, c[k].y, d);
+              if (l32 + d <= last) {
+                c[k].x += tx;
+                c[k].y += ty;
+              }
+            }
+          }
+        }
+        const int cell[4] = {cp0 + p, cp0 + 2 * H - 1 - p, cn0 + p, cn0 + 2 * H - 1 - p};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (head) {
+            float2* q = G + PADI(cell[k] & mask);
+            *q = cadd(*q, c[k]);
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  __syncthreads();  // every warp's grid complete
+  return mirror;
+}
+
 // ZF = false: input is the half image spectrum (image R2C over all axes) with
 // both lateral destinations of a row; ZF = true: input is the row's own full
 // depth spectrum Fbar[row][l mod nz].
@@ -858,6 +1072,14 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     const bool valid = row < P.rows;
     float2* X = smem + slot * P.slot;
     float4* N = nodes_all + slot * (P.nz + 2);
+    if (L.spread_mode == 3) {
+      float2* X2 = tpr >= 64 ? smem + L.grid2_off + slot * P.slot : nullptr;
+      const bool mirror = adjoint_pairs<H, ZF>(P, W, row, valid, lane, X, X2, N);
+      const float scale = (valid && !ZF && mirror) ? 0.5f : 1.0f;
+      float2* dst = const_cast<float2*>(P.pt) + (size_t)(valid ? row : 0) * nt;
+      fft_inverse_crop(X, M, P.mshift, nt, lane, tpr, L.tw, L.Mmax >> P.mshift, dst, P.prescale, scale, valid, X2);
+      continue;
+    }
     const int nzh = P.nz >> 1;
     RowGeom rg;
     int nneg = 1, nn = 0;

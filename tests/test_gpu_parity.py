@@ -426,14 +426,19 @@ def test_deterministic_spread(pai, g):
         torch.use_deterministic_algorithms(prev)
 
 
-@pytest.mark.parametrize("mode", ["atomic", "runs", "tap"])
+@pytest.mark.parametrize("mode", ["atomic", "runs", "tap", "pairs"])
 @pytest.mark.parametrize("g,method", [(ph.Geometry(dim=2, nx=96, nt=200, nz=80, dz=0.9), "kb"),
                                       (ph.Geometry(dim=3, nx=20, ny=16, nt=48, nz=24, dy=1.2), "kb"),
-                                      (ph.Geometry(dim=2, nx=64, nt=128, nz=64), "linear")],
-                         ids=["2d", "3d", "2d-linear"])
+                                      (ph.Geometry(dim=2, nx=64, nt=128, nz=64), "linear"),
+                                      (ph.Geometry(dim=2, nx=64, nt=400, nz=160, dz=1.1, c=1.3), "kb"),
+                                      (ph.Geometry(dim=3, nx=12, ny=10, nt=300, nz=40, dx=0.9), "kb")],
+                         ids=["2d", "3d", "2d-linear", "2d-m1024", "3d-m1024"])
 def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
-    """Both spreads, forced with PAI_SPREAD (the tuner may prefer either), for the
-    adjoint against the oracle's adjoint, and the forward model against its oracle."""
+    """Every spread, forced with PAI_SPREAD (the tuner may prefer any), for the
+    adjoint against the oracle's adjoint, and the forward model against its
+    oracle.  "pairs" (node pairs into warp-private grids) applies to rows of one
+    warp (padded length 512: 2d) or two warps (1024: the m1024 cases); the
+    others fall back to the tap phases."""
     import oracle.methods as om
     monkeypatch.setenv("PAI_SPREAD", mode)
     plan = pai.Plan(gdict(g, method=method, oversampling=2.0))
@@ -448,7 +453,24 @@ def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
         lhs = float(np.vdot(Rp, h.astype(np.float64).ravel()))
         rhs = float(np.vdot(p.astype(np.float64).ravel(), got.ravel()))
         assert abs(lhs - rhs) < 1e-6 * np.linalg.norm(Rp) * np.linalg.norm(h)
-    if method == "kb":
+    if method == "kb" and g.nt < 256:
         model = pai.ForwardModel(gdict(g, K=3))
         f = np.asarray(ph.random_image(32, g), np.float32)
         assert rel(to_np(model(to_gpu(f))), oracle.forward_model(g, f.astype(np.float64))) < TOL
+
+
+@pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+                               ph.Geometry(dim=3, nx=24, ny=20, nt=512, nz=96, dz=0.7)], ids=["m512", "m1024"])
+def test_pair_spread_repeats_bit_for_bit(pai, g, monkeypatch):
+    """The pair spread sums every grid cell in a fixed order (warp-private grids,
+    plain read-modify-writes separated by warp barriers): two calls give
+    identical bits, and it agrees with the atomic spread to FP32 rounding."""
+    import torch
+    h = to_gpu(ph.random_image(33, g))
+    monkeypatch.setenv("PAI_SPREAD", "pairs")
+    plan = pai.Plan(gdict(g, K=3))
+    a, b = plan.adjoint(h).clone(), plan.adjoint(h).clone()
+    assert torch.equal(a, b)
+    monkeypatch.setenv("PAI_SPREAD", "atomic")
+    ref = pai.Plan(gdict(g, K=3)).adjoint(h)
+    assert rel(to_np(a), to_np(ref)) < 1e-6
