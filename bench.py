@@ -290,6 +290,17 @@ def timed_steps(fn, reps, flush, stream):
     return sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / reps
 
 
+def window_summary(plan, count):
+    """The window the plan's tuner kept for a batch (taps, padded lengths,
+    oversampling, worst predicted error) and its tuning log."""
+    infos = [plan.problem_info(i) for i in range(count)]
+    return {"taps": sorted({i["taps"] for i in infos}),
+            "M_range": [min(i["M"] for i in infos), max(i["M"] for i in infos)],
+            "oversampling_range": [min(i["oversampling"] for i in infos), max(i["oversampling"] for i in infos)],
+            "max_predicted_error": max(i["predicted_error"] for i in infos),
+            "tuning_log": plan.tuning_log.strip().splitlines()}
+
+
 def compare_batched_plain(pai, geoms, p, out, batched_ms, flush, stream, reps=20):
     """The problems of a batched plan as separate single-problem plans run one
     after another on the same stream: graph-replayed plans (each plan replays
@@ -736,6 +747,7 @@ def main():
     batched = None
     if multi:
         batched = compare_batched_plain(pai, geoms, p, out, ms, flush, stream)
+        batched["window"] = window_summary(plan, len(geoms))
     elif args.config == "large2d" and not args.no_batched and rank == 0:
         # the default run also measures the batched half of the metric on the
         # 64-problem uneven batch (the headline value stays the single problem)
@@ -752,6 +764,7 @@ def main():
         batched["workload"] = f"batched2d: {bdesc}"
         batched["voxels_per_step"] = voxels_of(bgeoms)
         batched["batched_voxels_per_s"] = voxels_of(bgeoms) / (bms * 1e-3)
+        batched["window"] = window_summary(bplan, len(bgeoms))
         bplan.close()
         del bflat, bout
         torch.cuda.empty_cache()

@@ -137,8 +137,15 @@ pai_status pai_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t* out);
  * executed together: one lateral FFT per problem, ONE persistent row-kernel
  * launch over every lateral-frequency row of every problem, one inverse FFT
  * per problem, all replayed as one CUDA graph.  The problems share the tap
- * count (the largest over the batch) and the method (PAI_ERR_INVALID_ARG
- * otherwise); each keeps its own oversampling.
+ * count and the method (PAI_ERR_INVALID_ARG otherwise); each keeps its own
+ * oversampling.  When every problem leaves the window open (method KB, K,
+ * oversampling and alpha all 0) the plan times window candidates -- for each
+ * half tap count H, every problem's smallest power-of-two padded length whose
+ * truncation error stays within 1e-7 and whose prescale spans at most a
+ * factor 32 (low oversampling with many taps magnifies FP32 rounding) -- and
+ * keeps the fastest (see
+ * pai_tuning_log, pai_get_problem_info); otherwise the tap count is the
+ * largest the problems ask for.
  * Data and images of the batch are concatenated in g-order.                  */
 pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream, pai_plan_t* out);
 
@@ -218,8 +225,31 @@ pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream);
  * again on next use).  Any other value: PAI_ERR_INVALID_ARG.               */
 pai_status pai_set_deterministic(pai_plan_t plan, int deterministic);
 
-/* Fill *info with the plan's parameters.                                     */
+/* Fill *info with the plan's parameters (M, oversampling, K and alpha of
+ * problem 0; pai_get_problem_info gives them for every problem of a batch).  */
 pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info);
+
+/* The window and padded length one problem of a plan runs with (Algorithm 1
+ * parameters: c = M / nt, K = H / c with 2H taps, alpha = beta c).          */
+typedef struct {
+  int M;                  /* padded length of the oversampled temporal FFT      */
+  int taps;               /* window taps per node (2H; 2 linear, 1 nearest)     */
+  double oversampling;    /* c = M / nt                                        */
+  double K;               /* half interpolation length in omega units, H / c    */
+  double alpha;           /* Kaiser-Bessel shape (0 for other methods)          */
+  double predicted_error; /* truncation error of Fourmont's identity (-1: none) */
+} pai_problem_info;
+/* index: 0 <= index < pai_plan_info.count, else PAI_ERR_INVALID_ARG.        */
+pai_status pai_get_problem_info(pai_plan_t plan, int index, pai_problem_info* info);
+
+/* What the plan's tuner measured when the plan was built and what it kept:
+ * one line per measurement (window candidates: half tap count and padded
+ * lengths with the forward row kernel's time; CTA sizes; adjoint spread
+ * schemes; transform pipelines).  Copies at most cap - 1 bytes and a
+ * terminating NUL into buf (buf may be NULL when cap is 0); *len (may be
+ * NULL) receives the full length without the NUL.  Empty when the plan was
+ * built without tuning.                                                      */
+pai_status pai_tuning_log(pai_plan_t plan, char* buf, size_t cap, size_t* len);
 
 /* Cumulative count of kernels and cuFFT executions this plan has enqueued
  * (graph replays count the kernels inside the graph).                        */

@@ -23,7 +23,7 @@ from typing import Iterable, List, Optional, Sequence
 
 import torch
 
-__all__ = ["Plan", "ForwardModel", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "library_path", "load_library",
+__all__ = ["Plan", "ForwardModel", "PAIRecon", "PAIError", "Geometry", "PlanInfo", "ProblemInfo", "library_path", "load_library",
            "geometry", "window_probe", "cutoff_table", "cached_plan", "reconstruct", "adjoint"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +89,18 @@ class PlanInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ProblemInfo(ctypes.Structure):
+    """Mirror of ``pai_problem_info``."""
+
+    _fields_ = [
+        ("M", ctypes.c_int), ("taps", ctypes.c_int), ("oversampling", ctypes.c_double), ("K", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("predicted_error", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -132,6 +144,10 @@ def load_library() -> ctypes.CDLL:
         lib.pai_set_stream.restype = st
         lib.pai_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         lib.pai_get_info.restype = st
+        lib.pai_get_problem_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ProblemInfo)]
+        lib.pai_get_problem_info.restype = st
+        lib.pai_tuning_log.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        lib.pai_tuning_log.restype = st
         lib.pai_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         lib.pai_launch_count.restype = st
         lib.pai_destroy.argtypes = [vp]
@@ -412,6 +428,22 @@ class Plan:
         n = ctypes.c_longlong()
         _check(self._lib.pai_launch_count(self._h, ctypes.byref(n)), "pai_launch_count")
         return int(n.value)
+
+    def problem_info(self, index: int = 0) -> dict:
+        """Padded length, taps, oversampling, K, alpha and predicted window error of
+        problem ``index`` (``pai_get_problem_info``)."""
+        i = ProblemInfo()
+        _check(self._lib.pai_get_problem_info(self._h, int(index), ctypes.byref(i)), "pai_get_problem_info")
+        return i.as_dict()
+
+    @property
+    def tuning_log(self) -> str:
+        """What the tuner timed and kept when the plan was built (``pai_tuning_log``)."""
+        n = ctypes.c_size_t()
+        _check(self._lib.pai_tuning_log(self._h, None, 0, ctypes.byref(n)), "pai_tuning_log")
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(self._lib.pai_tuning_log(self._h, buf, n.value + 1, None), "pai_tuning_log")
+        return buf.value.decode()
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -39,6 +40,7 @@ struct ProblemHost {
   size_t pt_off = 0, fh_off = 0;      // complex values into the workspaces
   size_t pre_off = 0, rowS_off = 0, zt_off = 0;
   cufftHandle lat_r2c = 0, lat_c2r = 0, img_c2r = 0, img_r2c = 0;
+  bool made[4] = {false, false, false, false};  // which of the four handles cufftCreate made
   bool have_plans = false;
   bool own_lateral = false;  // lateral R2C by the library's own kernel (2-D, power-of-two nx)
   size_t data_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nt; }
@@ -109,6 +111,7 @@ struct pai_plan_s {
   cudaStream_t s_up = nullptr, s_down = nullptr;
   cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
   long long host_calls = 0;
+  bool pipe_ready = false;  // streams, staging pairs and events of the pipelined host calls exist
   // discrete forward model plans (pai_forward_plan): this plan's geometry is
   // the padded box; the image / detector geometry and the box buffers
   bool qmode = false;
@@ -120,6 +123,14 @@ struct pai_plan_s {
   int cut_R = 0;
   double cut_eps = 0.0;
   bool use_graph = true;
+  std::string tune_log;  // what the plan's tuner timed and kept, one line per measurement
+  // host-side failure injection for the tests of the error paths (set from
+  // the environment when the plan is built; see plan_malloc / plan_fft)
+  long long alloc_budget = -1;  // PAI_FAULT_ALLOC_BYTES: device bytes this plan may allocate (-1: no cap)
+  long long alloc_used = 0;
+  int fft_fail_at = -1;         // PAI_FAULT_CUFFT_PLAN: the n-th cuFFT plan creation (from 0) fails
+  int fft_made = 0;
+  size_t items_fwd_bytes = 0, items_adj_bytes = 0;
   std::vector<GraphEntry> graphs;
   long long own_kernels = 0, fft_execs = 0;
   int own_kernels_per_call = 0, fft_per_call = 0;
@@ -138,6 +149,35 @@ pai_status fft_status(cufftResult r) {
   if (r == CUFFT_SUCCESS) return PAI_OK;
   if (r == CUFFT_ALLOC_FAILED) return PAI_ERR_OOM;
   return PAI_ERR_CUFFT;
+}
+
+// Device allocation of a plan.  With an allocation cap set (failure
+// injection) a request beyond it fails like an exhausted device, before any
+// CUDA call, so the unwinding of a partly built plan can be tested without
+// exhausting a GPU.
+pai_status plan_malloc(pai_plan_s* P, void** ptr, size_t bytes) {
+  if (P->alloc_budget >= 0 && P->alloc_used + (long long)bytes > P->alloc_budget) return PAI_ERR_OOM;
+  const cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  P->alloc_used += (long long)bytes;
+  return PAI_OK;
+}
+
+// cuFFT plan creation of a plan; with PAI_FAULT_CUFFT_PLAN = n the n-th
+// creation (counted from 0 over the plan's build) reports a cuFFT failure
+// without calling cuFFT.
+cufftResult plan_fft(pai_plan_s* P, cufftHandle h, int rank, int* n, int* inem, int istride, int idist, int* onem,
+                     int ostride, int odist, cufftType type, int batch, size_t* ws) {
+  if (P->fft_made++ == P->fft_fail_at) return CUFFT_INTERNAL_ERROR;
+  return cufftMakePlanMany(h, rank, n, inem, istride, idist, onem, ostride, odist, type, batch, ws);
+}
+
+long long env_ll(const char* name, long long dflt) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const long long x = std::strtoll(v, &end, 10);
+  return (end && *end == 0) ? x : dflt;
 }
 
 #define PAI_TRY(x)                      \
@@ -162,7 +202,7 @@ pai_status choose_params(ProblemHost& p) {
   return PAI_OK;
 }
 
-pai_status make_cufft_plans(ProblemHost& p, size_t& work) {
+pai_status make_cufft_plans(pai_plan_s* P, ProblemHost& p, size_t& work) {
   const pai_geometry& g = p.g;
   size_t ws = 0;
   // lateral R2C / C2R: batch over time samples, element stride nt
@@ -175,12 +215,14 @@ pai_status make_cufft_plans(ProblemHost& p, size_t& work) {
       n[0] = g.nx; n[1] = g.ny; inem[0] = g.nx; inem[1] = g.ny; onem[0] = g.nx; onem[1] = g.ny / 2 + 1;
     }
     PAI_FFT(cufftCreate(&p.lat_r2c));
+    p.made[0] = true;
     PAI_FFT(cufftSetAutoAllocation(p.lat_r2c, 0));
-    PAI_FFT(cufftMakePlanMany(p.lat_r2c, rank, n, inem, g.nt, 1, onem, g.nt, 1, CUFFT_R2C, g.nt, &ws));
+    PAI_FFT(plan_fft(P, p.lat_r2c, rank, n, inem, g.nt, 1, onem, g.nt, 1, CUFFT_R2C, g.nt, &ws));
     work = std::max(work, ws);
     PAI_FFT(cufftCreate(&p.lat_c2r));
+    p.made[1] = true;
     PAI_FFT(cufftSetAutoAllocation(p.lat_c2r, 0));
-    PAI_FFT(cufftMakePlanMany(p.lat_c2r, rank, n, onem, g.nt, 1, inem, g.nt, 1, CUFFT_C2R, g.nt, &ws));
+    PAI_FFT(plan_fft(P, p.lat_c2r, rank, n, onem, g.nt, 1, inem, g.nt, 1, CUFFT_C2R, g.nt, &ws));
     work = std::max(work, ws);
   }
   // image C2R / R2C over all axes, natural layout, depth halved
@@ -193,24 +235,28 @@ pai_status make_cufft_plans(ProblemHost& p, size_t& work) {
       n[0] = g.nx; n[1] = g.ny; n[2] = g.nz;
     }
     PAI_FFT(cufftCreate(&p.img_c2r));
+    p.made[2] = true;
     PAI_FFT(cufftSetAutoAllocation(p.img_c2r, 0));
-    PAI_FFT(cufftMakePlanMany(p.img_c2r, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &ws));
+    PAI_FFT(plan_fft(P, p.img_c2r, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &ws));
     work = std::max(work, ws);
     PAI_FFT(cufftCreate(&p.img_r2c));
+    p.made[3] = true;
     PAI_FFT(cufftSetAutoAllocation(p.img_r2c, 0));
-    PAI_FFT(cufftMakePlanMany(p.img_r2c, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &ws));
+    PAI_FFT(plan_fft(P, p.img_r2c, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &ws));
     work = std::max(work, ws);
   }
   p.have_plans = true;
   return PAI_OK;
 }
 
+// Destroys every handle cufftCreate made, also those of a plan whose
+// construction failed half way.
 void destroy_fft(ProblemHost& p) {
-  if (!p.have_plans) return;
-  if (p.lat_r2c) cufftDestroy(p.lat_r2c);
-  if (p.lat_c2r) cufftDestroy(p.lat_c2r);
-  if (p.img_c2r) cufftDestroy(p.img_c2r);
-  if (p.img_r2c) cufftDestroy(p.img_r2c);
+  if (p.made[0]) cufftDestroy(p.lat_r2c);
+  if (p.made[1]) cufftDestroy(p.lat_c2r);
+  if (p.made[2]) cufftDestroy(p.img_c2r);
+  if (p.made[3]) cufftDestroy(p.img_r2c);
+  for (bool& m : p.made) m = false;
   p.have_plans = false;
 }
 
@@ -479,69 +525,139 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   PAI_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   const char* env_graph = std::getenv("PAI_USE_GRAPH");
   P->use_graph = !(env_graph && env_graph[0] == '0');
+  P->alloc_budget = env_ll("PAI_FAULT_ALLOC_BYTES", -1);
+  P->fft_fail_at = (int)env_ll("PAI_FAULT_CUFFT_PLAN", -1);
 
   // ---- parameters -------------------------------------------------------
   P->probs.resize(count);
-  double c_min = 1e30;
   for (int i = 0; i < count; ++i) {
     ProblemHost& p = P->probs[i];
     p.g = gs[i];
     if (p.g.dim == 2) { p.g.ny = 1; p.g.dy = 1.0; }
     PAI_TRY(choose_params(p));
-    P->H = std::max(P->H, p.H);
-    P->Mmax = std::max(P->Mmax, p.M);
-    c_min = std::min(c_min, p.c_eff);
   }
   P->method = gs[0].method;
-  if (P->method == PAI_METHOD_KB) {
-    // one window shape for the whole plan: common H and beta
-    bool user_alpha = count == 1 && gs[0].alpha > 0;
-    P->beta = user_alpha ? P->probs[0].beta : kPi * (2.0 - 1.0 / c_min) * (1.0 - 1e-3);
+  // The window of the whole plan from every problem's padded length M (set
+  // in p.M): a common half tap count (H > 0: that one; 0: the largest the
+  // problems chose) and, for Kaiser-Bessel, a common shape beta from the
+  // smallest oversampling, so one set of tap polynomials serves the launch.
+  auto set_window = [&](int Hc) -> pai_status {
+    P->H = 0;
+    P->Mmax = 0;
+    P->pred_err = 0.0;
+    double c_min = 1e30;
     for (auto& p : P->probs) {
-      p.H = P->H;
-      p.beta = P->beta;
-      p.K_eff = p.H / p.c_eff;
-      p.alpha_eff = p.beta * p.c_eff;
-      if (!(p.alpha_eff > kPi) || !(p.alpha_eff < kPi * (2 * p.c_eff - 1))) return PAI_ERR_INVALID_ARG;
-      p.pred_err = predicted_error(0, p.c_eff, p.H, p.beta);
-      P->pred_err = std::max(P->pred_err, p.pred_err);
+      p.mshift = 0;
+      while ((1 << p.mshift) < p.M) ++p.mshift;
+      p.c_eff = (double)p.M / p.g.nt;
+      P->H = std::max(P->H, Hc > 0 ? Hc : p.H);
+      P->Mmax = std::max(P->Mmax, p.M);
+      c_min = std::min(c_min, p.c_eff);
     }
-    P->fit_err = fit_window(0, P->H, P->beta, &P->poly);
-    if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
-  } else if (P->method == PAI_METHOD_TSINC) {
-    // the indicator window: a fixed shape, only the common tap count
-    P->beta = 0.0;
-    for (auto& p : P->probs) {
-      p.H = P->H;
-      p.beta = 0.0;
-      p.K_eff = p.H / p.c_eff;
-      p.alpha_eff = 0.0;
-      p.pred_err = predicted_error(1, p.c_eff, p.H, 0.0);
-      P->pred_err = std::max(P->pred_err, p.pred_err);
+    if (P->method == PAI_METHOD_KB) {
+      bool user_alpha = count == 1 && gs[0].alpha > 0;
+      P->beta = user_alpha ? P->probs[0].beta : default_beta(c_min);
+      for (auto& p : P->probs) {
+        p.H = P->H;
+        p.beta = P->beta;
+        p.K_eff = p.H / p.c_eff;
+        p.alpha_eff = p.beta * p.c_eff;
+        if (!window_shape_ok(p.c_eff, p.beta)) return PAI_ERR_INVALID_ARG;
+        p.pred_err = predicted_error(0, p.c_eff, p.H, p.beta);
+        P->pred_err = std::max(P->pred_err, p.pred_err);
+      }
+      P->fit_err = fit_window(0, P->H, P->beta, &P->poly);
+      if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
+    } else if (P->method == PAI_METHOD_TSINC) {
+      // the indicator window: a fixed shape, only the common tap count
+      P->beta = 0.0;
+      for (auto& p : P->probs) {
+        p.H = P->H;
+        p.beta = 0.0;
+        p.K_eff = p.H / p.c_eff;
+        p.alpha_eff = 0.0;
+        p.pred_err = predicted_error(1, p.c_eff, p.H, 0.0);
+        P->pred_err = std::max(P->pred_err, p.pred_err);
+      }
+      P->fit_err = fit_window(1, P->H, 0.0, &P->poly);
+      if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
+    } else {
+      // interpolation of the plain oversampled DFT: no window, no a-priori bound
+      P->beta = 0.0;
+      std::memset(&P->poly, 0, sizeof(P->poly));
+      P->fit_err = 0.0;
+      P->pred_err = -1.0;
+      for (auto& p : P->probs) {
+        p.H = P->H;
+        p.beta = 0.0;
+        p.K_eff = 0.0;
+        p.alpha_eff = 0.0;
+        p.pred_err = -1.0;
+      }
     }
-    P->fit_err = fit_window(1, P->H, 0.0, &P->poly);
-    if (!(P->fit_err < 1e-6)) return PAI_ERR_UNSUPPORTED;
-  } else {
-    // interpolation of the plain oversampled DFT: no window, no a-priori bound
-    P->beta = 0.0;
-    std::memset(&P->poly, 0, sizeof(P->poly));
-    P->fit_err = 0.0;
-    P->pred_err = -1.0;
-    for (auto& p : P->probs) {
-      p.H = P->H;
-      p.beta = 0.0;
-      p.K_eff = 0.0;
-      p.alpha_eff = 0.0;
-      p.pred_err = -1.0;
+    return PAI_OK;
+  };
+  PAI_TRY(set_window(0));
+  std::vector<int> rule_M(count);
+  for (int i = 0; i < count; ++i) rule_M[i] = P->probs[i].M;
+  const int rule_H = P->H;
+
+  // Window candidates for the tuner when the request leaves the window to the
+  // plan (Kaiser-Bessel, K, oversampling and alpha all 0): for each half tap
+  // count H, every problem takes the smallest power-of-two M whose
+  // oversampling keeps the truncation error within kAutoWindowTol under the
+  // common shape; the plan times the candidates and keeps the fastest.
+  struct WindowCandidate {
+    int H;
+    std::vector<int> M;
+  };
+  std::vector<WindowCandidate> cands;
+  bool auto_window = !qmode && P->method == PAI_METHOD_KB;
+  for (int i = 0; i < count; ++i)
+    if (gs[i].K != 0 || gs[i].oversampling != 0 || gs[i].alpha != 0) auto_window = false;
+  if (auto_window) {
+    for (int H = 3; H <= 8; ++H) {
+      std::vector<int> Ms(count);
+      bool ok = true;
+      for (int i = 0; i < count && ok; ++i) {
+        Ms[i] = smallest_padded_length(P->probs[i].g, H, kAutoWindowTol);
+        ok = Ms[i] > 0;
+      }
+      // the common shape comes from the smallest oversampling; raise any M
+      // whose problem then misses the bound (a few rounds at most)
+      for (int round = 0; ok && round < 8; ++round) {
+        double c_min = 1e30;
+        for (int i = 0; i < count; ++i) c_min = std::min(c_min, (double)Ms[i] / P->probs[i].g.nt);
+        const double beta = default_beta(c_min);
+        bool changed = false;
+        for (int i = 0; i < count && ok; ++i) {
+          const double c = (double)Ms[i] / P->probs[i].g.nt;
+          if (!window_shape_ok(c, beta) || predicted_error(0, c, H, beta) > kAutoWindowTol ||
+              prescale_range(c, H, beta) > kMaxPrescaleRange) {
+            Ms[i] *= 2;
+            ok = Ms[i] <= 16 * 1024;
+            changed = true;
+          }
+        }
+        if (!changed) break;
+        if (round == 7) ok = false;
+      }
+      if (!ok) continue;
+      bool dup = false;
+      for (auto& c : cands) dup = dup || c.M == Ms;
+      if (!dup) cands.push_back({H, Ms});
     }
   }
+  int tw_need = P->Mmax;
+  for (auto& c : cands)
+    for (int m : c.M) tw_need = std::max(tw_need, m);
 
   // ---- CTA shape ----------------------------------------------------------
   int sms = 0;
   PAI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
   int smem_optin = 0;
   PAI_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
-  const int tpr_max = P->Mmax / kElemsPerThread;
+  int tpr_max = P->Mmax / kElemsPerThread;
   const char* env_t = std::getenv("PAI_THREADS");
   int threads = env_t ? std::atoi(env_t) : 512;
   // forward-model plans (no tuner): the spread's barriers favour small CTAs
@@ -627,7 +743,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   std::vector<float> tables(tab_off, 0.0f);
   for (auto& p : P->probs)
     fill_row_tables(p.g, p.c_eff, p.H, p.beta, &tables[p.pre_off], &tables[p.rowS_off], &tables[p.zt_off]);
-  P->TW = P->Mmax;
+  P->TW = tw_need;  // covers every window candidate's padded length
   for (auto& p : P->probs) {
     p.own_lateral = p.g.dim == 2 && lateral_supported(p.g.nx, p.g.nt);
     if (p.own_lateral || P->zf) P->TW = std::max(P->TW, p.g.nx);
@@ -636,19 +752,18 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       if (p.g.dim == 3) P->TW = std::max(P->TW, p.g.ny);
     }
   }
-  std::vector<float2> tw(P->TW);
+  std::vector<float2> tw(twiddle_entries(P->TW));
   twiddle_table(P->TW, tw.data());
 
   // ---- device memory ------------------------------------------------------
-  PAI_CUDA(cudaMalloc(&P->d_pt, std::max<size_t>(pt_off, 1) * sizeof(float2)));
-  PAI_CUDA(cudaMalloc(&P->d_fh, std::max<size_t>(fh_off, 1) * sizeof(float2)));
-  PAI_CUDA(cudaMalloc(&P->d_tables, std::max<size_t>(tab_off, 4) * sizeof(float)));
-  PAI_CUDA(cudaMalloc(&P->d_tw, P->TW * sizeof(float2)));
-  PAI_CUDA(cudaMalloc(&P->d_problems, count * sizeof(RowProblem)));
-  PAI_CUDA(cudaMalloc(&P->d_counter, 4 * sizeof(int)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_pt, std::max<size_t>(pt_off, 1) * sizeof(float2)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_fh, std::max<size_t>(fh_off, 1) * sizeof(float2)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_tables, std::max<size_t>(tab_off, 4) * sizeof(float)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_tw, tw.size() * sizeof(float2)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_problems, count * sizeof(RowProblem)));
+  PAI_TRY(plan_malloc(P, (void**)&P->d_counter, 4 * sizeof(int)));
   PAI_CUDA(cudaMemcpy(P->d_tables, tables.data(), tab_off * sizeof(float), cudaMemcpyHostToDevice));
-  PAI_CUDA(cudaMemcpy(P->d_tw, tw.data(), P->TW * sizeof(float2), cudaMemcpyHostToDevice));
-  P->ws_bytes = (pt_off + fh_off + P->TW) * sizeof(float2) + tab_off * sizeof(float);
+  PAI_CUDA(cudaMemcpy(P->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
 
   std::vector<RowProblem> rp(count);
   for (int i = 0; i < count; ++i) {
@@ -668,7 +783,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
 
   // ---- cuFFT ----------------------------------------------------------------
   size_t work = 0;
-  for (auto& p : P->probs) PAI_TRY(make_cufft_plans(p, work));
+  for (auto& p : P->probs) PAI_TRY(make_cufft_plans(P, p, work));
   P->cufft_work = work;
   P->nbranch = std::min(count, 4);  // measured on the 64-problem batch: 4 beat 2, 6, 8, 16, 32
   if (P->nbranch > 1) {
@@ -679,7 +794,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     for (int b = 0; b < P->nbranch; ++b) {
       PAI_CUDA(cudaStreamCreateWithFlags(&P->branch[b], cudaStreamNonBlocking));
       PAI_CUDA(cudaEventCreateWithFlags(&P->ev_join[b], cudaEventDisableTiming));
-      if (work) PAI_CUDA(cudaMalloc(&P->branch_work[b], work));
+      if (work) PAI_TRY(plan_malloc(P, &P->branch_work[b], work));
     }
     for (size_t i = 0; i < P->probs.size(); ++i) {
       auto& p = P->probs[i];
@@ -689,10 +804,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
         PAI_FFT(cufftSetStream(h, P->branch[b]));
       }
     }
-    P->ws_bytes += work * P->nbranch;
   } else {
     if (work) {
-      PAI_CUDA(cudaMalloc(&P->d_cufft_work, work));
+      PAI_TRY(plan_malloc(P, &P->d_cufft_work, work));
       for (auto& p : P->probs) {
         PAI_FFT(cufftSetWorkArea(p.lat_r2c, P->d_cufft_work));
         PAI_FFT(cufftSetWorkArea(p.lat_c2r, P->d_cufft_work));
@@ -700,7 +814,6 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
         PAI_FFT(cufftSetWorkArea(p.img_r2c, P->d_cufft_work));
       }
     }
-    P->ws_bytes += work;
   }
   PAI_TRY(set_fft_streams(P, P->stream));
 
@@ -739,9 +852,11 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     build_items(T, items);
     P->nitems_fwd = (int)items.size();
     P->ctas = std::min(P->nitems_fwd, occ_f * sms);
+    if (P->d_items_fwd) P->alloc_used -= (long long)P->items_fwd_bytes;
     cudaFree(P->d_items_fwd);
     P->d_items_fwd = nullptr;
-    PAI_CUDA(cudaMalloc(&P->d_items_fwd, items.size() * sizeof(WorkItem)));
+    P->items_fwd_bytes = items.size() * sizeof(WorkItem);
+    PAI_TRY(plan_malloc(P, (void**)&P->d_items_fwd, P->items_fwd_bytes));
     PAI_CUDA(cudaMemcpy(P->d_items_fwd, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
     PAI_CUDA(cudaMemcpy(P->d_problems, rp.data(), count * sizeof(RowProblem), cudaMemcpyHostToDevice));
     return PAI_OK;
@@ -806,15 +921,86 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->ctas_adj = std::min(P->nitems_adj, occ_a * sms);
     P->ctas_adj3 = std::min(P->nitems_adj, P->ctas_adj3);
     if (P->d_items_adj == P->d_items_fwd) P->d_items_adj = nullptr;
+    if (P->d_items_adj) P->alloc_used -= (long long)P->items_adj_bytes;
     cudaFree(P->d_items_adj);
     P->d_items_adj = nullptr;
-    PAI_CUDA(cudaMalloc(&P->d_items_adj, items.size() * sizeof(WorkItem)));
+    P->items_adj_bytes = items.size() * sizeof(WorkItem);
+    PAI_TRY(plan_malloc(P, (void**)&P->d_items_adj, P->items_adj_bytes));
     PAI_CUDA(cudaMemcpy(P->d_items_adj, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
     return PAI_OK;
   };
-  // ---- tuner: pick the CTA size by timing the forward row kernel -------------
   const char* env_tune = std::getenv("PAI_AUTOTUNE");
   bool tune = !(env_tune && env_tune[0] == '0') && !env_t && !qmode;
+  char logline[512];
+  // ---- tuner: the window (half tap count and every problem's padded length) ---
+  // (the candidates above and the fixed rule's choice, each timed as one
+  // forward row-kernel launch over the whole plan)
+  if (tune && !cands.empty()) {
+    bool have_rule = false;
+    for (auto& c : cands) have_rule = have_rule || (c.H == rule_H && c.M == rule_M);
+    if (!have_rule) cands.insert(cands.begin(), WindowCandidate{rule_H, rule_M});
+    std::vector<float> tables_c(tab_off, 0.0f);
+    auto apply = [&](const WindowCandidate& c) -> pai_status {
+      for (int i = 0; i < count; ++i) P->probs[i].M = c.M[i];
+      PAI_TRY(set_window(c.H));
+      for (int i = 0; i < count; ++i) {
+        ProblemHost& p = P->probs[i];
+        p.tpr = p.M / kElemsPerThread;
+        fill_row_tables(p.g, p.c_eff, p.H, p.beta, &tables_c[p.pre_off], &tables_c[p.rowS_off], &tables_c[p.zt_off]);
+        fill_row_scalars(p.g, p.M, rp[i]);
+      }
+      PAI_CUDA(cudaMemcpy(P->d_tables, tables_c.data(), tab_off * sizeof(float), cudaMemcpyHostToDevice));
+      tpr_max = P->Mmax / kElemsPerThread;
+      return PAI_OK;
+    };
+    cudaEvent_t e0, e1;
+    PAI_CUDA(cudaEventCreate(&e0));
+    PAI_CUDA(cudaEventCreate(&e1));
+    PAI_CUDA(cudaMemset(P->d_pt, 0, pt_off * sizeof(float2)));
+    int best_i = -1;
+    float best_ms = 1e30f;
+    for (size_t k = 0; k < cands.size(); ++k) {
+      if (apply(cands[k]) != PAI_OK) continue;
+      const int T = std::min(1024, std::max(512, tpr_max));
+      if (finish_shape(T) != PAI_OK) continue;
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, P->cap_stream);
+        if (enqueue_row(P, false, P->cap_stream, T, P->ctas, P->smem_fwd, P->zf) != PAI_OK) break;
+        cudaEventRecord(e1, P->cap_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+      }
+      long long msum = 0;
+      int mmin = 1 << 30, mmax = 0;
+      for (int m : cands[k].M) {
+        msum += m;
+        mmin = std::min(mmin, m);
+        mmax = std::max(mmax, m);
+      }
+      std::snprintf(logline, sizeof logline,
+                    "window: H=%d (taps %d), padded lengths %d..%d (sum %lld), max predicted error %.2e%s: "
+                    "forward row kernel %.4f ms\n",
+                    cands[k].H, 2 * cands[k].H, mmin, mmax, msum, P->pred_err,
+                    (cands[k].H == rule_H && cands[k].M == rule_M) ? " [fixed rule]" : "", best);
+      P->tune_log += logline;
+      if (best < best_ms) {
+        best_ms = best;
+        best_i = (int)k;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    PAI_TRY(apply(cands[best_i >= 0 ? best_i : 0]));
+    threads = std::max(threads, tpr_max);
+    if (threads > 1024) return PAI_ERR_UNSUPPORTED;
+    std::snprintf(logline, sizeof logline, "window: kept H=%d\n", P->H);
+    P->tune_log += logline;
+  }
+  // ---- tuner: pick the CTA size by timing the forward row kernel -------------
   if (tune) {
     int best_T = 0;
     float best_ms = 1e30f;
@@ -835,6 +1021,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) best = std::min(best, ms);
       }
+      std::snprintf(logline, sizeof logline, "forward CTA: %d threads: forward row kernel %.4f ms\n", T, best);
+      P->tune_log += logline;
       if (best < best_ms) { best_ms = best; best_T = T; }
     }
     cudaEventDestroy(e0);
@@ -871,6 +1059,8 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) best = std::min(best, ms);
       }
+      std::snprintf(logline, sizeof logline, "adjoint CTA: %d threads: adjoint row kernel %.4f ms\n", T, best);
+      P->tune_log += logline;
       if (best < best_ms) { best_ms = best; best_T = T; }
     }
     cudaEventDestroy(e0);
@@ -917,6 +1107,13 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
+    static const char* kSpreadName[4] = {"tap phases", "atomics per node", "atomics per run", "node pairs"};
+    for (int mode = 0; mode < 4; ++mode)
+      if (best_ms[mode] < 1e29f) {
+        std::snprintf(logline, sizeof logline, "adjoint spread: %s: adjoint row kernel %.4f ms\n", kSpreadName[mode],
+                      best_ms[mode]);
+        P->tune_log += logline;
+      }
     P->spread_tuned = 0;
     for (int mode = 1; mode < 4; ++mode)
       if (best_ms[mode] < best_ms[P->spread_tuned]) P->spread_tuned = mode;
@@ -958,6 +1155,10 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
         else (variant == 0 ? ms_zf : ms_cufft) = best;
       }
       P->zf_adj = adj_zf <= adj_cufft;
+      std::snprintf(logline, sizeof logline,
+                    "pipeline: forward pass %.4f ms with the library's transforms, %.4f ms with cuFFT; adjoint "
+                    "%.4f / %.4f ms\n", ms_zf, ms_cufft, adj_zf, adj_cufft);
+      P->tune_log += logline;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       set_fft_streams(P, P->stream);
@@ -974,7 +1175,6 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       P->fft_per_call = 2 * count - own_lat;
     }
   }
-  P->ws_bytes += (size_t)P->nitems_fwd * sizeof(WorkItem);
   if (P->zf) {
     int k = 1;  // the row kernel
     for (auto& p : P->probs) k += (p.g.dim == 2) ? 3 : 5;  // lateral forward + depth FFT + lateral inverse
@@ -996,6 +1196,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->fft_per_adj = 2 * count;
   }
   PAI_CUDA(cudaDeviceSynchronize());
+  P->ws_bytes = (size_t)P->alloc_used;  // every device buffer the plan holds
   guard.p = nullptr;
   *out = P;
   return PAI_OK;
@@ -1088,9 +1289,16 @@ pai_status pai_reconstruct_host(pai_plan_t plan, const float* h_p, float* h_f) {
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
   pai_status st = PAI_OK;
-  if (!plan->d_stage_in) {
-    st = cuda_status(cudaMalloc(&plan->d_stage_in, plan->data_total * sizeof(float)));
-    if (st == PAI_OK) st = cuda_status(cudaMalloc(&plan->d_stage_out, plan->img_total * sizeof(float)));
+  if (!plan->d_stage_in || !plan->d_stage_out) {
+    st = plan_malloc(plan, (void**)&plan->d_stage_in, plan->data_total * sizeof(float));
+    if (st == PAI_OK) st = plan_malloc(plan, (void**)&plan->d_stage_out, plan->img_total * sizeof(float));
+    if (st != PAI_OK) {
+      // leave no half-made staging pair behind: the next call starts over
+      if (plan->d_stage_in) plan->alloc_used -= (long long)(plan->data_total * sizeof(float));
+      cudaFree(plan->d_stage_in);
+      plan->d_stage_in = nullptr;
+      plan->d_stage_out = nullptr;
+    }
   }
   if (st == PAI_OK)
     st = cuda_status(cudaMemcpyAsync(plan->d_stage_in, h_p, plan->data_total * sizeof(float),
@@ -1116,16 +1324,23 @@ pai_status pai_reconstruct_host_async(pai_plan_t plan, const float* h_p, float* 
   cudaGetDevice(&prev);
   if (prev != plan->device) cudaSetDevice(plan->device);
   pai_status st = PAI_OK;
-  if (!plan->s_up) {
-    st = cuda_status(cudaStreamCreateWithFlags(&plan->s_up, cudaStreamNonBlocking));
-    if (st == PAI_OK) st = cuda_status(cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking));
+  if (!plan->pipe_ready) {
+    if (!plan->s_up) st = cuda_status(cudaStreamCreateWithFlags(&plan->s_up, cudaStreamNonBlocking));
+    if (st == PAI_OK && !plan->s_down) st = cuda_status(cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking));
     for (int k = 0; k < 2 && st == PAI_OK; ++k) {
-      st = cuda_status(cudaMalloc(&plan->d_pipe_in[k], plan->data_total * sizeof(float)));
-      if (st == PAI_OK) st = cuda_status(cudaMalloc(&plan->d_pipe_out[k], plan->img_total * sizeof(float)));
-      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_up[k], cudaEventDisableTiming));
-      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_comp[k], cudaEventDisableTiming));
-      if (st == PAI_OK) st = cuda_status(cudaEventCreateWithFlags(&plan->ev_down[k], cudaEventDisableTiming));
+      if (!plan->d_pipe_in[k]) st = plan_malloc(plan, (void**)&plan->d_pipe_in[k], plan->data_total * sizeof(float));
+      if (st == PAI_OK && !plan->d_pipe_out[k])
+        st = plan_malloc(plan, (void**)&plan->d_pipe_out[k], plan->img_total * sizeof(float));
+      if (st == PAI_OK && !plan->ev_up[k])
+        st = cuda_status(cudaEventCreateWithFlags(&plan->ev_up[k], cudaEventDisableTiming));
+      if (st == PAI_OK && !plan->ev_comp[k])
+        st = cuda_status(cudaEventCreateWithFlags(&plan->ev_comp[k], cudaEventDisableTiming));
+      if (st == PAI_OK && !plan->ev_down[k])
+        st = cuda_status(cudaEventCreateWithFlags(&plan->ev_down[k], cudaEventDisableTiming));
     }
+    // a failed set-up keeps what it made (released with the plan) and is
+    // completed by the next call
+    plan->pipe_ready = st == PAI_OK;
   }
   const int k = (int)(plan->host_calls & 1);
   const bool reuse = plan->host_calls >= 2;  // events of call k-2 exist
@@ -1247,6 +1462,30 @@ pai_status pai_get_info(pai_plan_t plan, pai_plan_info* info) {
   return PAI_OK;
 }
 
+pai_status pai_get_problem_info(pai_plan_t plan, int index, pai_problem_info* info) {
+  if (!plan || !info || index < 0 || index >= (int)plan->probs.size()) return PAI_ERR_INVALID_ARG;
+  const ProblemHost& p = plan->probs[index];
+  info->M = p.M;
+  info->taps = plan->method == PAI_METHOD_LINEAR ? 2 : plan->method == PAI_METHOD_NEAREST ? 1 : 2 * plan->H;
+  info->oversampling = p.c_eff;
+  info->K = p.K_eff;
+  info->alpha = p.alpha_eff;
+  info->predicted_error = p.pred_err;
+  return PAI_OK;
+}
+
+pai_status pai_tuning_log(pai_plan_t plan, char* buf, size_t cap, size_t* len) {
+  if (!plan || (cap > 0 && !buf)) return PAI_ERR_INVALID_ARG;
+  const std::string& t = plan->tune_log;
+  if (len) *len = t.size();
+  if (cap > 0) {
+    const size_t n = std::min(cap - 1, t.size());
+    std::memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return PAI_OK;
+}
+
 pai_status pai_launch_count(pai_plan_t plan, long long* kernels) {
   if (!plan || !kernels) return PAI_ERR_INVALID_ARG;
   *kernels = plan->own_kernels;
@@ -1292,12 +1531,13 @@ pai_status pai_forward_plan(const pai_geometry* g, void* cuda_stream, pai_plan_t
   PAI_TRY(build_plan(&gb, 1, cuda_stream, &P, true));
   P->qimg = gi;
   const size_t box_img = (size_t)gb.nx * gb.ny * gb.nz, box_dat = (size_t)gb.nx * gb.ny * gb.nt;
-  pai_status st = cuda_status(cudaMalloc(&P->d_qin, box_img * sizeof(float)));
-  if (st == PAI_OK) st = cuda_status(cudaMalloc(&P->d_qout, box_dat * sizeof(float)));
+  pai_status st = plan_malloc(P, (void**)&P->d_qin, box_img * sizeof(float));
+  if (st == PAI_OK) st = plan_malloc(P, (void**)&P->d_qout, box_dat * sizeof(float));
   if (st != PAI_OK) {
     release(P);
     return st == PAI_ERR_CUDA ? PAI_ERR_OOM : st;
   }
+  P->ws_bytes = (size_t)P->alloc_used;
   *out = P;
   return PAI_OK;
 }
@@ -1383,7 +1623,7 @@ pai_status pai_set_cutoff(pai_plan_t plan, double eps) {
     cutoff_table(g.dim, eps, w);
     std::vector<float> wf(w.begin(), w.end());
     float* d = nullptr;
-    st = cuda_status(cudaMalloc(&d, wf.size() * sizeof(float)));
+    st = plan_malloc(plan, (void**)&d, wf.size() * sizeof(float));
     if (st == PAI_OK) st = cuda_status(cudaMemcpy(d, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
     if (st == PAI_OK) {
       plan->d_cut = d;

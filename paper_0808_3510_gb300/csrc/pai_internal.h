@@ -13,6 +13,19 @@ namespace pai {
 
 // Largest half tap count supported by the row kernels: taps per node = 2H <= 24.
 constexpr int kMaxH = 12;
+// Truncation-error bound of the window the tuner picks when the request leaves
+// it open (K, oversampling and alpha 0).  The bound is on the error of
+// Fourmont's identity, i.e. relative to the sum of the row's magnitudes; a
+// row's relative L2 error can exceed it by up to about sqrt(nt) when its
+// samples cancel, so 1e-7 keeps every spectrum row within the 1e-5 agreement
+// required with the direct reconstruction for nt up to 16384 (measured: a
+// 1e-6 bound let one row of the 64-problem batch reach 2e-5).
+constexpr double kAutoWindowTol = 1e-7;
+// Largest prescale dynamic range (prescale_range) the tuner accepts: FP32
+// errors grow about as 1e-8 times the range (measured: 3e-7 at range 8 with
+// c = 2, 16 taps; 4e-5 at range 5600 with c = 1.2, 16 taps), so 32 keeps them
+// near 1e-6, a tenth of the required agreement.
+constexpr double kMaxPrescaleRange = 32.0;
 // Polynomial degree of each tap's window polynomial in z = frac - 1/2.
 // Even part: z^0, z^2, ..., z^6 (4 coefficients); odd part: z^1, ..., z^7.
 // Degree 7 fits the Kaiser-Bessel taps as closely as degree 9 does once the
@@ -56,7 +69,6 @@ struct RowProblem {
   int nzshift;             // log2(nz) when nz is a power of two, else 0
   int method;              // PAI_METHOD_*
   int qmode;               // adjoint kernel evaluates the discrete forward model (depth-row layout only)
-  int zslot = 0;           // complex values per row slot of the fused depth transform (nz + nz/32 + 4)
 };
 
 struct WorkItem {
@@ -73,8 +85,6 @@ struct RowLaunch {
   int Mmax;
   int H;                       // half tap count (taps = 2H)
   int fft_region;              // complex values of shared memory used by the row slots (adjoint: nodes follow)
-  int zdepth_off = 0;          // forward depth-row layout: complex offset of the fused depth-transform lines
-                               // (0 = not fused: the kernel writes the depth spectrum F[row][l])
   // adjoint only: sorted-bin spread buffers
   int chunk;                   // nodes per bin chunk
   int bin_offset;              // bytes from the start of dynamic shared memory to the bins
@@ -102,6 +112,11 @@ double window_s(int kind, double theta, double c, int H, double beta);
 double fit_window(int kind, int H, double beta, WindowPoly* out);
 // Truncation error of Fourmont's identity for (c, H, beta), max over theta and offsets.
 double predicted_error(int kind, double c, int H, double beta);
+// Dynamic range of the Kaiser-Bessel prescale over theta in [-pi, pi]:
+// s(pi) / s(0) = I0(H beta) / I0(H sqrt(beta^2 - (pi/c)^2)).  The FP32 FFT of
+// the prescaled samples carries rounding errors relative to its largest
+// values, so the reconstruction's FP32 error grows about in proportion.
+double prescale_range(double c, int H, double beta);
 // Prescale for sample n: s(theta_n) * phi(0) * extra, theta_n = 2 pi n/nt - pi.
 void prescale_table(int kind, int nt, double c, int H, double beta, double extra, float* out);
 
@@ -115,6 +130,14 @@ struct ProblemParams {
 void split_ff(double v, float& hi, float& lo);
 int validate_geometry(const pai_geometry& g);
 int choose_problem_params(const pai_geometry& g, ProblemParams& p);
+// Kaiser-Bessel shape for oversampling c: beta = pi (2 - 1/c) (1 - 1e-3) (alpha = beta c
+// slightly below pi (2c - 1)), and the Lemma's condition pi < beta c < pi (2c - 1).
+double default_beta(double c_eff);
+int window_shape_ok(double c_eff, double beta);
+// Smallest power-of-two padded length M > nt (at least 32, at most 16384) whose
+// oversampling c = M / nt and default shape give a truncation error <= tol with
+// half tap count H; 0 if there is none.
+int smallest_padded_length(const pai_geometry& g, int H, double tol);
 // Lateral axes (n1, n2) with n2 halved by the R2C transform, and their spacings.
 void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d2);
 // prescale [nt], rowS [2 * rows] (float-float), zt [4 * (nz/2 + 1)].
@@ -125,7 +148,13 @@ inline int method_window(int method) { return method == PAI_METHOD_TSINC ? 1 : 0
 inline bool method_interp(int method) { return method == PAI_METHOD_LINEAR || method == PAI_METHOD_NEAREST; }
 // Scalar fields of RowProblem (everything except pointers and rpc).
 void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r);
-void twiddle_table(int Mmax, float2* tw);
+// Two-level twiddle table for transforms of every length dividing TW (a power
+// of two): tw[j] = w^j for j < kTwLo, tw[kTwLo + i] = w^(kTwLo i) for
+// i < TW / kTwLo, w = e^{-2 pi i / TW}; w^k = tw[kTwLo + (k >> 6)] tw[k & 63].
+constexpr int kTwLoShift = 6;
+constexpr int kTwLo = 1 << kTwLoShift;
+inline int twiddle_entries(int TW) { return kTwLo + (TW > kTwLo ? TW / kTwLo : 1); }
+void twiddle_table(int TW, float2* tw);
 
 // zf selects the depth-fused kernels (see pai_row_kernels.cuh).
 cudaError_t launch_row_forward(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem,

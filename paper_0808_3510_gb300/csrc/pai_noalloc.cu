@@ -79,7 +79,7 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   const size_t o_prob = off;  off = align256(off + sizeof(RowProblem));
   const size_t o_items = off; off = align256(off + (size_t)nitems * sizeof(WorkItem));
   const size_t o_count = off; off = align256(off + sizeof(int));
-  const size_t o_tw = off;    off = align256(off + (size_t)pp.M * sizeof(float2));
+  const size_t o_tw = off;    off = align256(off + (size_t)twiddle_entries(pp.M) * sizeof(float2));
   const size_t o_pre = off;   off = align256(off + (size_t)g.nt * sizeof(float));
   const size_t o_rows = off;  off = align256(off + (size_t)rows * 2 * sizeof(float));
   const size_t o_zt = off;    off = align256(off + (size_t)(g.nz / 2 + 1) * 4 * sizeof(float));

@@ -95,6 +95,23 @@ int choose_problem_params(const pai_geometry& g, ProblemParams& p) {
   return PAI_OK;
 }
 
+int window_shape_ok(double c_eff, double beta) {
+  // the Lemma's condition on the shape alpha = beta c: pi < alpha < pi (2c - 1)
+  const double a = beta * c_eff;
+  return a > kPi && a < kPi * (2 * c_eff - 1);
+}
+
+double default_beta(double c_eff) { return kPi * (2.0 - 1.0 / c_eff) * (1.0 - 1e-3); }
+
+int smallest_padded_length(const pai_geometry& g, int H, double tol) {
+  for (long long M = std::max<long long>(32, next_pow2((long long)g.nt + 1)); M <= 16 * 1024; M <<= 1) {
+    const double c = (double)M / g.nt;
+    const double beta = default_beta(c);
+    if (predicted_error(0, c, H, beta) <= tol && prescale_range(c, H, beta) <= kMaxPrescaleRange) return (int)M;
+  }
+  return 0;
+}
+
 void lateral_axes(const pai_geometry& g, int& n1, int& n2, double& d1, double& d2) {
   if (g.dim == 2) {
     n1 = 1; n2 = g.nx; d1 = 1.0; d2 = g.dx;
@@ -155,11 +172,14 @@ void fill_row_scalars(const pai_geometry& g, int M, RowProblem& r) {
   r.method = g.method;
 }
 
-void twiddle_table(int Mmax, float2* tw) {
-  for (int k = 0; k < Mmax; ++k) {
-    double a = -2.0 * kPi * k / Mmax;
-    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+void twiddle_table(int TW, float2* tw) {
+  auto w = [&](long long k) {
+    const double a = -2.0 * kPi * (double)(k % TW) / TW;
+    return make_float2((float)std::cos(a), (float)std::sin(a));
+  };
+  for (int j = 0; j < kTwLo; ++j) tw[j] = w(j);
+  const int nhi = twiddle_entries(TW) - kTwLo;
+  for (int i = 0; i < nhi; ++i) tw[kTwLo + i] = w((long long)kTwLo * i);
 }
 
 }  // namespace pai

@@ -172,12 +172,21 @@ struct TwBase {
   float2 b[R >= 16 ? 4 : R >= 8 ? 3 : R >= 4 ? 2 : 1];
 };
 
+// The twiddle table is two-level (twiddle_table): w^k = hi[k >> 6] lo[k & 63]
+// with lo = tw[0..63] and hi = tw[64..], w = e^{-2 pi i / TW}.  Both parts
+// together hold 64 + TW/64 values (2.5 KB at TW = 16384), so they stay in L1
+// while a full-length table (64 KB at TW = 8192) would miss there; the
+// product costs one complex multiply and about one extra rounding.
+__device__ __forceinline__ float2 tw_at(const float2* __restrict__ tw, int k) {
+  return cmul(__ldg(&tw[kTwLo + (k >> kTwLoShift)]), __ldg(&tw[k & (kTwLo - 1)]));
+}
+
 template <int R>
 __device__ __forceinline__ void tw_load(TwBase<R>& t, const float2* __restrict__ tw, int step) {
-  t.b[0] = __ldg(&tw[step]);
-  if (R >= 4) t.b[1] = __ldg(&tw[2 * step]);
-  if (R >= 8) t.b[2] = __ldg(&tw[4 * step]);
-  if (R >= 16) t.b[3] = __ldg(&tw[8 * step]);
+  t.b[0] = tw_at(tw, step);
+  if (R >= 4) t.b[1] = tw_at(tw, 2 * step);
+  if (R >= 8) t.b[2] = tw_at(tw, 4 * step);
+  if (R >= 16) t.b[3] = tw_at(tw, 8 * step);
 }
 
 template <bool INV>
@@ -770,15 +779,12 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
 // for 0 < |l| < nz/2, F[0] = 0 (l = 0 rule), F[-nz/2] = W (P(+|K|) + P(-|K|))/2
 // (Nyquist rule).  One task per |l| evaluates the node pair.  An inverse depth
 // FFT of each line followed by the lateral C2R completes Eq. (fft-1).
-// PAD: Zs is a shared-memory line in the padded FFT layout (F[l] at
-// Zs[PADI(l)]), the input of the fused depth transform.
-template <int H, bool PAD = false>
+template <int H>
 __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPoly& W, const float2* X, float2* Zs,
                                              int row, int lane) {
   const float2 S = P.rowS[row];
   const int nzh = P.nz >> 1;
-  auto at = [&](int l) -> float2& { return PAD ? Zs[PADI(l)] : Zs[l]; };
-  if (lane == 0) at(0) = make_float2(0.f, 0.f);
+  if (lane == 0) Zs[0] = make_float2(0.f, 0.f);
   float4 zt_next = __ldg(&P.zt[min(lane, nzh - 1) + 1]);
   for (int i = lane; i < nzh; i += P.tpr) {
     const int lp = i + 1;
@@ -791,10 +797,10 @@ __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPo
     float2 v, u;
     node_value_pair<H>(P, X, W, j0, fr, v, u);
     if (lp == nzh) {
-      at(nzh) = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
+      Zs[nzh] = make_float2(0.5f * wt * (v.x + u.x), 0.5f * wt * (v.y + u.y));
     } else {
-      at(lp) = make_float2(wt * v.x, wt * v.y);
-      at(P.nz - lp) = make_float2(wt * u.x, wt * u.y);
+      Zs[lp] = make_float2(wt * v.x, wt * v.y);
+      Zs[P.nz - lp] = make_float2(wt * u.x, wt * u.y);
     }
   }
 }
@@ -828,19 +834,7 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
     fft_first_pass_from_global(X, M, P.nt, lane, tpr, P.pt + (size_t)(valid ? row : 0) * P.nt, P.prescale);
     fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
-    if (ZF && L.zdepth_off > 0) {
-      // fused depth transform: the row's depth spectrum goes to shared memory,
-      // is inverse transformed there (nz / 16 active threads) and the depth
-      // line h[row][z] = sum_l e^{+2 pi i l z / nz} F[l] is written out
-      float2* Fz = smem + L.zdepth_off + slot * P.zslot;
-      if (valid) gather_row_z<H, true>(P, W, X, Fz, row, lane);
-      const int tz = P.nz / kElemsPerThread;
-      fft_smem<true, kLayoutFlat>(Fz, P.nz, P.nzshift, lane, tz, L.tw, L.Mmax >> P.nzshift, lane < tz);
-      if (valid) {
-        float2* h = P.fh + (size_t)row * P.nz;
-        for (int z = lane; z < P.nz; z += tpr) h[z] = Fz[z];
-      }
-    } else if (valid) {
+    if (valid) {
       if (!ZF) gather_row<H>(P, W, X, row, lane);
       else gather_row_z<H>(P, W, X, P.fh + (size_t)row * P.nz, row, lane);
     }

@@ -164,6 +164,13 @@ double predicted_error(int kind, double c, int H, double beta) {
   return worst;
 }
 
+double prescale_range(double c, int H, double beta) {
+  const double pi = 3.14159265358979323846;
+  const double edge = beta * beta - (pi / c) * (pi / c);
+  if (!(edge > 0)) return 1e300;
+  return bessel_i0(H * beta) / bessel_i0(H * std::sqrt(edge));
+}
+
 void prescale_table(int kind, int nt, double c, int H, double beta, double extra, float* out) {
   const double pi = 3.14159265358979323846;
   const double peak = window_phi(kind, 0.0, H, beta);

@@ -191,3 +191,24 @@ def test_noalloc_rejects_oversized_tables_on_the_host(pai):
     # a geometry that fits reaches the pointer check instead
     small = pai.geometry(dict(dim=2, nx=16, nt=64, nz=32))
     assert lib.pai_spectrum_rows_noalloc(ctypes.byref(small), None, None, None) == 1
+
+
+def test_failure_injection_settings_are_harmless_without_a_device(pai, monkeypatch):
+    """The allocation cap and the forced cuFFT failure are read when a plan is
+    built; invalid geometries are still rejected first, on the host, with the
+    out-pointer untouched."""
+    monkeypatch.setenv("PAI_FAULT_ALLOC_BYTES", "0")
+    monkeypatch.setenv("PAI_FAULT_CUFFT_PLAN", "0")
+    lib = pai.load_library()
+    g = pai.geometry(dict(dim=2, nx=15, nt=32, nz=16))
+    h = ctypes.c_void_p(0x5EED)
+    assert lib.pai_plan(ctypes.byref(g), None, ctypes.byref(h)) == 1
+    assert h.value == 0x5EED
+
+
+def test_problem_info_and_tuning_log_validate_arguments(pai):
+    lib = pai.load_library()
+    info = pai.ProblemInfo()
+    assert lib.pai_get_problem_info(None, 0, ctypes.byref(info)) == 1
+    n = ctypes.c_size_t()
+    assert lib.pai_tuning_log(None, None, 0, ctypes.byref(n)) == 1

@@ -210,10 +210,16 @@ def test_batched_64_full_size_sampled_rows(pai):
     """The 64-problem batch at full size (nx = 2 U{128..1024}, nt = 2 U{256..2048},
     nz = nt/2; the benchmark's batched workload and launch): for every problem,
     three spectrum rows of the one batched launch against the oracle's row-by-row
-    direct sums, and the images of four problems against FP64 inverse FFTs of
-    the GPU's own spectra."""
+    direct sums, the images of four problems against FP64 inverse FFTs of the
+    GPU's own spectra, and the whole images of three problems (the cheapest,
+    the one of median cost and a seeded pick below 8 G oracle operations)
+    against the oracle's direct reconstruction."""
     geoms = ph.batched_2d_geometries(0, 64)
     rng = np.random.default_rng(11)
+    cost = [g.nx * (g.nx * g.nt + g.nz * g.nt) + 2 * g.nx * g.nz * (g.nx + g.nz) for g in geoms]
+    order = np.argsort(cost)
+    cheap = [i for i in range(64) if cost[i] < 8e9]
+    full = {int(order[0]), int(order[32]), int(cheap[int(rng.integers(len(cheap)))])}
     datas = [rng.standard_normal(g.data_shape).astype(np.float32) for g in geoms]
     plan = pai.Plan([gdict(g) for g in geoms])
     flat = to_gpu(np.concatenate([d.ravel() for d in datas]))
@@ -236,6 +242,8 @@ def test_batched_64_full_size_sampled_rows(pai):
         if i % 16 == 0:
             ref = np.fft.irfft2(Si.astype(np.complex128) * (g.nx * g.nz), s=(g.nx, g.nz))
             assert rel(fi, ref) < TOL, i
+        if i in full:
+            assert rel(fi, oracle.reconstruct(g, d.astype(np.float64))) < TOL, i
     assert so == S.size and fo == f.size
 
 
@@ -256,11 +264,27 @@ def test_largest_padded_length(pai, method):
     assert rel(f, ref) < TOL
 
 
+_LARGE_ORACLE = {}
+
+
+def _large_oracle_image(g, p):
+    """The oracle's full direct reconstruction of the 2-D large workload (direct
+    lateral DFT, direct NUDFT at all 2048 x 2048 nodes, weight, direct inverse
+    DFT; about 50 G FP64 complex MACs on the host's cores), computed once per
+    test session and shared by both pipelines."""
+    key = (g.nx, g.nt, g.nz, float(p[0, 0]), float(p[-1, -1]))
+    if key not in _LARGE_ORACLE:
+        _LARGE_ORACLE[key] = oracle.reconstruct(g, p.astype(np.float64))
+    return _LARGE_ORACLE[key]
+
+
 def test_large_2d_sampled_rows(pai, pipeline):
     """2-D large (2048 x 4096 -> 2048 x 2048, c = 2, K = 4) in the launch
     configuration the benchmark times: sampled spectrum rows against the
-    oracle's row-by-row direct sums, and the image against an FP64 inverse FFT
-    of the GPU's own spectrum (checks the inverse stage at full size)."""
+    oracle's row-by-row direct sums, and the whole 2048 x 2048 image against the
+    oracle's direct reconstruction (its own inverse DFT of its own spectrum),
+    plus an FP64 inverse FFT of the GPU's own spectrum (the inverse stage
+    alone)."""
     import torch
     g = ph.Geometry(dim=2, nx=2048, nt=4096, nz=2048)
     p = ph.random_data(40, g).astype(np.float32)
@@ -279,6 +303,7 @@ def test_large_2d_sampled_rows(pai, pipeline):
     f = to_np(plan.reconstruct(pt))
     ref = np.fft.irfft2(S.astype(np.complex128) * (g.nx * g.nz), s=(g.nx, g.nz))
     assert rel(f, ref) < TOL
+    assert rel(f, _large_oracle_image(g, p)) < TOL
 
 
 @pytest.mark.parametrize("shape", [(64, 48, 32), (32, 64, 64), (256, 64, 128)])
@@ -474,3 +499,34 @@ def test_pair_spread_repeats_bit_for_bit(pai, g, monkeypatch):
     monkeypatch.setenv("PAI_SPREAD", "atomic")
     ref = pai.Plan(gdict(g, K=3)).adjoint(h)
     assert rel(to_np(a), to_np(ref)) < 1e-6
+
+
+def test_window_tuner_on_a_batch(pai):
+    """With the window left open (K, oversampling and alpha 0) the plan times
+    window candidates and keeps one: every problem's padded length is a power of
+    two above nt with a truncation error <= 1e-7 under the common tap count and
+    shape, the tuning log lists the timed candidates, and the batch matches the
+    oracle problem by problem."""
+    rng = np.random.default_rng(17)
+    geoms = []
+    for _ in range(6):
+        nt = 4 * int(rng.integers(20, 100))
+        geoms.append(ph.Geometry(dim=2, nx=2 * int(rng.integers(16, 64)), nt=nt, nz=nt // 2))
+    plan = pai.Plan([gdict(g) for g in geoms])
+    log = plan.tuning_log
+    assert log.count("window: H=") >= 2 and "window: kept H=" in log, log
+    taps = {plan.problem_info(i)["taps"] for i in range(len(geoms))}
+    assert len(taps) == 1
+    for i, g in enumerate(geoms):
+        info = plan.problem_info(i)
+        M = info["M"]
+        assert M > g.nt and M & (M - 1) == 0
+        assert info["predicted_error"] <= 1e-7
+        assert abs(info["oversampling"] - M / g.nt) < 1e-12
+    ps = [ph.random_data(400 + i, g).astype(np.float32) for i, g in enumerate(geoms)]
+    out = to_np(plan.reconstruct(to_gpu(np.concatenate([p.ravel() for p in ps]))))
+    off = 0
+    for g, p in zip(geoms, ps):
+        n = g.nx * g.nz
+        assert rel(out[off: off + n].reshape(g.image_shape), oracle.reconstruct(g, p.astype(np.float64))) < TOL
+        off += n
