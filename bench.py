@@ -710,30 +710,44 @@ def main():
     st = plan.profile_stages(p, out, reps=50)
     st_adj = plan.profile_stages(out, grad, reps=20, adjoint=True) if grad_mode else None
     info = plan.info
+    # algorithmic bytes of the row kernel: the scope table's per-node figure for
+    # the gather with the weight (each oversampled-spectrum element inside some
+    # node's tap window read once, 8 B written per node: about 20 B per node in
+    # the half-lateral layout) times the nodes one launch evaluates; and, beside
+    # it, the fused kernel's own input and output (lateral spectrum rows in,
+    # half image spectrum out), which is all it moves through HBM
     nbytes_alg = 0
+    nbytes_io = 0
     for g in geoms:
         nl = g["nx"] * (g["ny"] if g["dim"] == 3 else 1)
         half = (g["ny"] if g["dim"] == 3 else g["nx"]) // 2 + 1
         rows = (g["nx"] if g["dim"] == 3 else 1) * half
-        nbytes_alg += rows * g["nt"] * 8 + nl * (g["nz"] // 2 + 1) * 8
+        nbytes_alg += 20 * nl * g["nz"]
+        nbytes_io += rows * g["nt"] * 8 + nl * (g["nz"] // 2 + 1) * 8
     peak, peak_src = hbm_peak()
     achieved = nbytes_alg / (st[1] * 1e-3) / 1e9
+    achieved_io = nbytes_io / (st[1] * 1e-3) / 1e9
     # ALU view of the same launch: 5 M log2 M flops per row FFT; per +-nu pair task
-    # 16 H (tap accumulation: two nodes x 2H taps x 2 FMA) + 20 H (per tap pair two
-    # 5-term polynomials in z^2 and the two weights) + 40 (node position, phase,
+    # 16 H (tap accumulation: two nodes x 2H taps x 2 FMA) + 16 H (per tap pair two
+    # 4-term polynomials in z^2 and the two weights) + 40 (node position, phase,
     # weight) flops
-    H = max(info["taps"] // 2, 1)
     flops = 0
-    for g in geoms:
+    for i, g in enumerate(geoms):
+        pinfo = plan.problem_info(i)
+        H = max(pinfo["taps"] // 2, 1)
+        M = pinfo["M"]
         half = (g["ny"] if g["dim"] == 3 else g["nx"]) // 2 + 1
         rows = (g["nx"] if g["dim"] == 3 else 1) * half
-        M = info["M"] if len(geoms) == 1 else 1 << math.ceil(math.log2(max(32, 2 * g["nt"])))
-        flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (36 * H + 40))
+        flops += rows * (5 * M * math.log2(M) + (g["nz"] // 2 + 1) * (32 * H + 40))
     fp32_peak, fp32_src = fp32_fma_peak(dev, clocks)
     roofline = {"bound": "hbm", "kernel": "row_forward (prescale + oversampled FFT + KB gather + weight)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(args.config), "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": nbytes_alg, "kernel_ms": st[1],
+                "algorithmic_bytes_per_launch": nbytes_alg,
+                "algorithmic_bytes": "20 B per node (gather + weight, half-lateral layout) x nodes per launch",
+                "fused_io": {"bytes_per_launch": nbytes_io, "achieved": achieved_io, "frac": achieved_io / peak,
+                             "what": "lateral spectrum rows in + half image spectrum out"},
+                "kernel_ms": st[1],
                 "stage_ms": {"lateral_fft": st[0], "row_kernel": st[1], "inverse_fft": st[2]},
                 "alu_view": {"flops_per_launch": flops, "achieved_tflops": flops / (st[1] * 1e-3) / 1e12,
                              "peak_tflops": fp32_peak, "frac": flops / (st[1] * 1e-3) / 1e12 / fp32_peak,
@@ -823,6 +837,7 @@ def main():
             "parity": parity,
             "roofline": roofline,
             "batched_vs_plain": batched,
+            "tuning_log": plan.tuning_log.strip().splitlines(),
             "step": "gradient of 0.5||R p - f||^2 (reconstruct + residual + adjoint)" if grad_mode else "reconstruct",
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -18,6 +18,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -70,7 +72,6 @@ struct pai_plan_s {
   int spread_tuned = 1;                             // the faster spread found when the plan was built
   int spread_det = 0;                               // the faster deterministic spread (0 or 3)
   bool pairs_ok = false;                            // spread mode 3 applies to every problem of the plan
-  int grid2_off = 0;                                // mode 3: complex offset of the second grids (0 = none)
   size_t smem_adj3 = 0;                             // mode 3: shared memory of the adjoint row kernel
   int ctas_adj3 = 0;                                //         and its CTA count
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
@@ -329,7 +330,6 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.bin_offset = P->bin_offset;
   L.bin_slot = P->bin_slot;
   L.spread_mode = P->spread_mode;
-  L.grid2_off = P->grid2_off;
   return L;
 }
 
@@ -337,7 +337,7 @@ pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads,
                        bool zf = false) {
   RowLaunch L = make_launch(P, adjoint);
   if (adjoint && P->spread_mode == 3) {
-    // the pair spread's second grids follow the node lists
+    // the pair-spread kernel's own occupancy gives its CTA count
     smem = P->smem_adj3;
     ctas = P->ctas_adj3;
   }
@@ -506,6 +506,32 @@ pai_status run(pai_plan_s* P, const void* in, void* out, bool adjoint) {
   }
   if (prev != P->device) cudaSetDevice(prev);
   return st;
+}
+
+// What the tuner decided for a set of geometries on a device, kept for the
+// process so that later plans of the same geometries make the same choices
+// (same results bit for bit, no tuning time): the window (half tap count and
+// padded lengths), the CTA sizes, the adjoint's spread and the pipelines.
+struct Wisdom {
+  int H = 0;
+  std::vector<int> M;  // empty: the window was not tuned
+  int threads = 0, threads_adj = 0, spread_tuned = 1, spread_det = 0;
+  bool zf = false, zf_adj = false;
+  std::string log;
+};
+std::mutex g_wisdom_mutex;
+std::map<std::string, Wisdom> g_wisdom;
+
+std::string wisdom_key(int device, const pai_geometry* gs, int count) {
+  std::string k = std::to_string(device) + ":" + std::to_string(count);
+  char buf[512];
+  for (int i = 0; i < count; ++i) {
+    const pai_geometry& g = gs[i];
+    std::snprintf(buf, sizeof buf, "|%d %d %d %a %a %d %a %a %d %a %a %a %a %d", g.dim, g.nx, g.ny, g.dx, g.dy, g.nt,
+                  g.dt, g.c, g.nz, g.dz, g.oversampling, g.K, g.alpha, g.method);
+    k += buf;
+  }
+  return k;
 }
 
 // Plan construction shared by pai_plan and pai_plan_batched.
@@ -846,7 +872,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->fft_region = (int)(region / sizeof(float2));
     P->smem_fwd = region;
     if (P->smem_fwd > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
-    const int occ_f = row_kernel_max_ctas_per_sm(false, T, P->smem_fwd, P->H, P->zf);
+    const int occ_f = row_kernel_max_ctas_per_sm(0, T, P->smem_fwd, P->H, P->zf);
     if (occ_f < 1) return PAI_ERR_UNSUPPORTED;
     std::vector<WorkItem> items;
     build_items(T, items);
@@ -888,30 +914,22 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->bin_offset = (int)(region + (size_t)node_cap * sizeof(float4));
     P->smem_adj = (size_t)P->bin_offset;
     if (P->smem_adj > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
-    const int occ_a = row_kernel_max_ctas_per_sm(true, T, P->smem_adj, P->H, P->zf);
+    const int occ_a = row_kernel_max_ctas_per_sm(1, T, P->smem_adj, P->H, P->zf);
     if (occ_a < 1) return PAI_ERR_UNSUPPORTED;
-    // spread mode 3 (node pairs into warp-private grids): windowed methods,
-    // rows of one or two warps, and 32 consecutive pairs spanning fewer than
-    // M - 2H cells (consecutive nodes of one sign are at most M c dt / (nz dz)
-    // cells apart)
+    // spread mode 3 (node pairs spread by one warp per row): windowed
+    // methods, rows of one or two warps, and 32 consecutive pairs spanning
+    // fewer than M - 2H cells (consecutive nodes of one sign are at most
+    // M c dt / (nz dz) cells apart)
     P->pairs_ok = !method_interp(P->method) && std::getenv("PAI_NO_PAIRS") == nullptr;
-    bool two_warps = false;
     for (auto& p : P->probs) {
       const double g1 = std::ceil((double)p.M * p.g.c * p.g.dt / (p.g.nz * p.g.dz)) + 1.0;
       if (p.tpr != 32 && p.tpr != 64) P->pairs_ok = false;
       if (!(32.0 * g1 + 2.0 * P->H + 2.0 < (double)p.M)) P->pairs_ok = false;
-      two_warps = two_warps || p.tpr == 64;
     }
-    P->grid2_off = 0;
     P->smem_adj3 = P->smem_adj;
     P->ctas_adj3 = 0;
     if (P->pairs_ok) {
-      if (two_warps) {
-        P->grid2_off = P->bin_offset / (int)sizeof(float2);
-        P->smem_adj3 = (size_t)P->bin_offset + region;
-      }
-      const int occ3 = P->smem_adj3 <= (size_t)smem_optin
-                           ? row_kernel_max_ctas_per_sm(true, T, P->smem_adj3, P->H, P->zf) : 0;
+      const int occ3 = row_kernel_max_ctas_per_sm(2, T, P->smem_adj3, P->H, P->zf);
       if (occ3 < 1) P->pairs_ok = false;
       P->ctas_adj3 = occ3 * sms;
     }
@@ -932,15 +950,26 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   const char* env_tune = std::getenv("PAI_AUTOTUNE");
   bool tune = !(env_tune && env_tune[0] == '0') && !env_t && !qmode;
   char logline[512];
+  // an earlier plan of the same geometries on this device: reuse its choices
+  const char* env_wis = std::getenv("PAI_WISDOM");
+  const bool use_wisdom = tune && !(env_wis && env_wis[0] == '0');
+  const std::string wkey = use_wisdom ? wisdom_key(P->device, gs, count) : std::string();
+  Wisdom wis;
+  bool have_wis = false;
+  if (use_wisdom) {
+    std::lock_guard<std::mutex> lock(g_wisdom_mutex);
+    auto it = g_wisdom.find(wkey);
+    if (it != g_wisdom.end()) {
+      wis = it->second;
+      have_wis = true;
+    }
+  }
+  if (have_wis) P->tune_log = "reused the choices of an earlier plan of the same geometries on this device:\n" + wis.log;
   // ---- tuner: the window (half tap count and every problem's padded length) ---
   // (the candidates above and the fixed rule's choice, each timed as one
   // forward row-kernel launch over the whole plan)
-  if (tune && !cands.empty()) {
-    bool have_rule = false;
-    for (auto& c : cands) have_rule = have_rule || (c.H == rule_H && c.M == rule_M);
-    if (!have_rule) cands.insert(cands.begin(), WindowCandidate{rule_H, rule_M});
-    std::vector<float> tables_c(tab_off, 0.0f);
-    auto apply = [&](const WindowCandidate& c) -> pai_status {
+  std::vector<float> tables_c(tab_off, 0.0f);
+  auto apply = [&](const WindowCandidate& c) -> pai_status {
       for (int i = 0; i < count; ++i) P->probs[i].M = c.M[i];
       PAI_TRY(set_window(c.H));
       for (int i = 0; i < count; ++i) {
@@ -952,7 +981,15 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
       PAI_CUDA(cudaMemcpy(P->d_tables, tables_c.data(), tab_off * sizeof(float), cudaMemcpyHostToDevice));
       tpr_max = P->Mmax / kElemsPerThread;
       return PAI_OK;
-    };
+  };
+  if (tune && !cands.empty() && have_wis && (int)wis.M.size() == count) {
+    PAI_TRY(apply(WindowCandidate{wis.H, wis.M}));
+    threads = std::max(threads, tpr_max);
+    if (threads > 1024) return PAI_ERR_UNSUPPORTED;
+  } else if (tune && !cands.empty()) {
+    bool have_rule = false;
+    for (auto& c : cands) have_rule = have_rule || (c.H == rule_H && c.M == rule_M);
+    if (!have_rule) cands.insert(cands.begin(), WindowCandidate{rule_H, rule_M});
     cudaEvent_t e0, e1;
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
@@ -1001,7 +1038,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->tune_log += logline;
   }
   // ---- tuner: pick the CTA size by timing the forward row kernel -------------
-  if (tune) {
+  if (tune && have_wis) {
+    threads = std::max(wis.threads, tpr_max);
+  } else if (tune) {
     int best_T = 0;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -1039,7 +1078,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // ---- tuner: the adjoint row kernel's CTA size, timed the same way ----------
   // (the spread's barriers and the forward's FFT passes favour different sizes)
   int threads_adj = threads;
-  if (tune) {
+  if (tune && have_wis) {
+    threads_adj = std::max(wis.threads_adj, tpr_max);
+  } else if (tune) {
     int best_T = 0;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -1085,6 +1126,9 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   P->spread_det = P->pairs_ok ? 3 : 0;
   if (env_mode >= 0) {
     P->spread_tuned = env_mode;
+  } else if (have_wis) {
+    P->spread_tuned = wis.spread_tuned == 3 && !P->pairs_ok ? 0 : wis.spread_tuned;
+    P->spread_det = wis.spread_det == 3 && !P->pairs_ok ? 0 : wis.spread_det;
   } else if (tune || qmode) {
     cudaEvent_t e0, e1;
     PAI_CUDA(cudaEventCreate(&e0));
@@ -1123,7 +1167,10 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   // ---- tuner: when both pipelines apply, keep the faster one ----------------
   // (library kernels for every stage vs cuFFT for the inverse and the adjoint's
   // image-side and data-side transforms), timed on one eager forward pass each
-  if (P->zf && tune) {
+  if (P->zf && tune && have_wis) {
+    P->zf = wis.zf;
+    P->zf_adj = wis.zf_adj;
+  } else if (P->zf && tune) {
     float* d_in = nullptr;
     float* d_out = nullptr;
     float ms_zf = 1e30f, ms_cufft = 1e30f;
@@ -1197,6 +1244,22 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   }
   PAI_CUDA(cudaDeviceSynchronize());
   P->ws_bytes = (size_t)P->alloc_used;  // every device buffer the plan holds
+  if (use_wisdom && !have_wis) {
+    Wisdom w;
+    if (!cands.empty()) {
+      w.H = P->H;
+      for (auto& p : P->probs) w.M.push_back(p.M);
+    }
+    w.threads = P->threads;
+    w.threads_adj = P->threads_adj;
+    w.spread_tuned = P->spread_tuned;
+    w.spread_det = P->spread_det;
+    w.zf = P->zf;
+    w.zf_adj = P->zf_adj;
+    w.log = P->tune_log;
+    std::lock_guard<std::mutex> lock(g_wisdom_mutex);
+    g_wisdom.emplace(wkey, std::move(w));
+  }
   guard.p = nullptr;
   *out = P;
   return PAI_OK;

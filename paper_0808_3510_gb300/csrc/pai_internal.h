@@ -91,9 +91,8 @@ struct RowLaunch {
   int bin_slot;                // bytes of bins per row slot: chunk * (2H+1) complex, 16-aligned
   int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics per
                                // node, 2 shared-memory atomics per run of nodes with equal j0, 3 node pairs
-                               // into warp-private grids (deterministic; windowed methods, 32 or 64 threads
-                               // per row)
-  int grid2_off = 0;           // spread mode 3 with two warps per row: complex offset of the second grids
+                               // spread by one warp per row (deterministic; windowed methods, 32 or 64
+                               // threads per row)
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)
@@ -175,7 +174,8 @@ cudaError_t launch_lateral_c2c(const float2* in, float2* out, int L, int C, int 
 // In-place FFT of `rows` contiguous complex lines of power-of-two length L (32 <= L <= 16384).
 cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const float2* tw, int twstride,
                             cudaStream_t s);
-int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H, bool zf = false);
+// kind: 0 forward row kernel, 1 adjoint row kernel, 2 adjoint row kernel with the pair spread
+int row_kernel_max_ctas_per_sm(int kind, int threads, size_t smem, int H, bool zf = false);
 
 // Data cutoff w_cut (pai_cutoff.cu).  R = ceil(sqrt(eps)); the table holds
 // (R+1)^dim weights indexed by the clipped distances to the faces, time last.

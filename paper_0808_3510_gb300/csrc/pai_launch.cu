@@ -6,7 +6,7 @@ namespace pai {
 #define PAI_UNIT(lo)                                                                                          \
   cudaError_t row_forward_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t, bool); \
   cudaError_t row_adjoint_h##lo(int, const RowLaunch&, const WindowPoly&, int, int, size_t, cudaStream_t, bool); \
-  int row_occupancy_h##lo(int, bool, int, size_t, bool);
+  int row_occupancy_h##lo(int, int, int, size_t, bool);
 PAI_UNIT(2)
 PAI_UNIT(5)
 PAI_UNIT(7)
@@ -35,11 +35,11 @@ cudaError_t launch_row_adjoint(const RowLaunch& L, const WindowPoly& w, int thre
   return row_adjoint_h9(H, L, w, threads, ctas, smem, s, zf);
 }
 
-int row_kernel_max_ctas_per_sm(bool adjoint, int threads, size_t smem, int H, bool zf) {
-  if (H < 5) return row_occupancy_h2(H, adjoint, threads, smem, zf);
-  if (H < 7) return row_occupancy_h5(H, adjoint, threads, smem, zf);
-  if (H < 9) return row_occupancy_h7(H, adjoint, threads, smem, zf);
-  return row_occupancy_h9(H, adjoint, threads, smem, zf);
+int row_kernel_max_ctas_per_sm(int kind, int threads, size_t smem, int H, bool zf) {
+  if (H < 5) return row_occupancy_h2(H, kind, threads, smem, zf);
+  if (H < 7) return row_occupancy_h5(H, kind, threads, smem, zf);
+  if (H < 9) return row_occupancy_h7(H, kind, threads, smem, zf);
+  return row_occupancy_h9(H, kind, threads, smem, zf);
 }
 
 }  // namespace pai

@@ -136,7 +136,7 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   L.H = pp.H;
   const size_t smem = row_fft_region_bytes(threads, pp.M);
   L.fft_region = (int)(smem / sizeof(float2));
-  const int occ = row_kernel_max_ctas_per_sm(false, threads, smem, pp.H);
+  const int occ = row_kernel_max_ctas_per_sm(0, threads, smem, pp.H);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAI_ERR_CUDA;
   if (occ < 1) return PAI_ERR_UNSUPPORTED;

@@ -40,13 +40,20 @@ static cudaError_t fwd_h(const RowLaunch& L, const WindowPoly& w, int threads, i
 template <int H>
 static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem, cudaStream_t s,
                          bool zf) {
+  if (L.spread_mode == 3)
+    return zf ? launch_k(row_adjoint_pairs_kernel<H, true>, L, w, threads, ctas, smem, s)
+              : launch_k(row_adjoint_pairs_kernel<H, false>, L, w, threads, ctas, smem, s);
   return zf ? launch_k(row_adjoint_kernel<H, true>, L, w, threads, ctas, smem, s)
             : launch_k(row_adjoint_kernel<H, false>, L, w, threads, ctas, smem, s);
 }
 
+// kind: 0 forward, 1 adjoint, 2 adjoint with the pair spread
 template <int H>
-static int occ_h(bool adjoint, int threads, size_t smem, bool zf) {
-  if (adjoint)
+static int occ_h(int kind, int threads, size_t smem, bool zf) {
+  if (kind == 2)
+    return zf ? occ_k(row_adjoint_pairs_kernel<H, true>, threads, smem)
+              : occ_k(row_adjoint_pairs_kernel<H, false>, threads, smem);
+  if (kind == 1)
     return zf ? occ_k(row_adjoint_kernel<H, true>, threads, smem) : occ_k(row_adjoint_kernel<H, false>, threads, smem);
   return zf ? occ_k(row_forward_kernel<H, true>, threads, smem) : occ_k(row_forward_kernel<H, false>, threads, smem);
 }
@@ -72,8 +79,8 @@ cudaError_t PAI_FN(row_adjoint)(int H, const RowLaunch& L, const WindowPoly& w, 
   return cudaErrorNotSupported;
 }
 
-int PAI_FN(row_occupancy)(int H, bool adjoint, int threads, size_t smem, bool zf) {
-  PAI_ALL(occ_h, adjoint, threads, smem, zf)
+int PAI_FN(row_occupancy)(int H, int kind, int threads, size_t smem, bool zf) {
+  PAI_ALL(occ_h, kind, threads, smem, zf)
   return -1;
 }
 

@@ -232,11 +232,9 @@ __device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
 // PADI(a + 16 r) = PADI(a) + 16 r + r/2 (r < 16).  Both hold for every pass
 // after the first radix-16 one (Ns = 16 or a multiple of 256), and for the
 // first pass (Ns = 1) PADI(16 j + r) = PADI(16 j) + r.
-// ADD2: the pass reads X + X2 (two padded grids of the same layout summed on
-// load) and writes its outputs to X.
-template <int R, bool INV, int OUT, bool ADD2 = false>
+template <int R, bool INV, int OUT>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
-                                         int twstride, bool active = true, const float2* X2 = nullptr) {
+                                         int twstride, bool active = true) {
   constexpr int NB = kElemsPerThread / R;
   float2 v[NB][R];
   TwBase<R> t[NB];
@@ -254,11 +252,6 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
         const float2* src = X + PADI(lane + i * tpr);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i][r] = src[r * rs];
-        if (ADD2) {
-          const float2* src2 = X2 + PADI(lane + i * tpr);
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[i][r] = cadd(v[i][r], src2[r * rs]);
-        }
       }
     } else {
 #pragma unroll
@@ -266,10 +259,6 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
         const int j = lane + i * tpr;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i][r] = X[PADI(j + r * MR)];
-        if (ADD2) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[i][r] = cadd(v[i][r], X2[PADI(j + r * MR)]);
-        }
       }
     }
   }
@@ -408,21 +397,12 @@ __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane,
 // kept, and only those 8 outputs are computed: with w = e^{+2 pi i/16},
 // A = inverse DFT8 of the even inputs and B of the odd,
 // Y[t] = A[t] + w^t B[t] (t = 0..3) and Y[t+8] = A[t] - w^t B[t] (t = 4..7).
-// X2 != nullptr: the input is the sum of the grids X and X2 (added as the
-// first pass loads them).
 __device__ __forceinline__ void fft_inverse_crop(float2* X, int M, int mshift, int nt, int lane, int tpr,
                                                  const float2* __restrict__ tw, int twstride, float2* dst,
-                                                 const float* __restrict__ prescale, float scale, bool valid,
-                                                 const float2* X2 = nullptr) {
+                                                 const float* __restrict__ prescale, float scale, bool valid) {
   int Ns = 1;
   const int r0 = mshift & 3;
-  if (X2) {
-    if (r0 == 3) fft_pass<8, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
-    else if (r0 == 2) fft_pass<4, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
-    else if (r0 == 1) fft_pass<2, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
-    else fft_pass<16, true, kLayoutPadded, true>(X, M, 1, lane, tpr, tw, twstride, true, X2);
-    Ns = r0 == 3 ? 8 : r0 == 2 ? 4 : r0 == 1 ? 2 : 16;
-  } else if (r0 == 3) {
+  if (r0 == 3) {
     fft_pass<8, true, kLayoutPadded>(X, M, 1, lane, tpr, tw, twstride);
     Ns = 8;
   } else if (r0 == 2) {
@@ -867,7 +847,7 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
 
-// Adjoint of one row by node pairs and warp-private grids (spread mode 3,
+// Adjoint of one row by node pairs spread by one warp (spread mode 3,
 // windowed methods, row slots of one or two warps).
 //
 // Phase 1: pair i holds the node pair +-x of one depth index (l = i + 1, or
@@ -878,22 +858,22 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
 // the forward gather takes it, so its tap q weighs w_{2H-1-q}(z), z = fr - 1/2:
 // one evaluation of the tap-pair polynomials serves both nodes.
 //
-// Phase 2: warp w of the row slot spreads the pairs [w np / nw, (w+1) np / nw)
-// into its own grid (warp 0: the row slot X, warp 1: X2), so no two warps
-// ever write one grid.  Within a warp 32 consecutive pairs go at a time, one
-// per lane; pairs with equal j0 form a run (the list is sorted), and for each
-// tap pair and each of the four contributions (taps p and 2H-1-p of +x and
-// of -x) the run's terms are summed across its lanes (segmented shuffle sum,
-// only when the 32 pairs hold a run) and the run's first lane adds the sum to
-// its cell with a plain read-modify-write.  Within one such step distinct
-// runs have distinct j0, hence distinct cells (the 32 pairs span fewer than
-// M - 2H cells, checked by the plan); a __syncwarp separates the steps.
-// Every cell therefore receives its terms in a fixed order: the result is
-// bit-repeatable.  The inverse FFT then reads X + X2.
+// Phase 2: the row slot's first warp spreads all pairs into the grid X, 32
+// consecutive pairs at a time, one per lane (with a second warp in the slot,
+// as for M = 1024, that warp waits: a private grid for it cost more in
+// occupancy than it saved); pairs with equal j0 form a run (the list is
+// sorted), and for each tap pair and each of the four contributions (taps p
+// and 2H-1-p of +x and of -x) the run's terms are summed across its lanes
+// (segmented shuffle sum, only when the 32 pairs hold a run) and the run's
+// first lane adds the sum to its cell with a plain read-modify-write.  Within
+// one such step distinct runs have distinct j0, hence distinct cells (the 32
+// pairs span fewer than M - 2H cells, checked by the plan); a __syncwarp
+// separates the steps.  Every cell therefore receives its terms in a fixed
+// order: the result is bit-repeatable.
 // Returns whether the row is a mirror row (non-ZF input, both destinations).
 template <int H, bool ZF>
 __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowPoly& W, int row, bool valid, int lane,
-                                              float2* X, float2* X2, float4* A) {
+                                              float2* X, float4* A) {
   const int tpr = P.tpr, M = P.M, nt = P.nt, mask = M - 1;
   const int nzh = P.nz >> 1;
   float2* B = reinterpret_cast<float2*>(A + nzh + 1);
@@ -978,14 +958,17 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
     }
   }
   __syncthreads();  // pair lists complete (every row slot)
-  const int nw = tpr >> 5;  // warps in the row slot (1 or 2)
+  // the row slot's first warp spreads every pair; a second warp (rows of
+  // 64 threads) waits at the barrier below
   const int w = lane >> 5, l32 = lane & 31;
-  float2* G = w == 0 ? X : X2;
-  for (int g = l32; g < M; g += 32) G[PADI(g)] = make_float2(0.f, 0.f);
-  __syncwarp();
-  if (valid) {
+  float2* G = X;
+  if (w == 0) {
+    for (int g = l32; g < M; g += 32) G[PADI(g)] = make_float2(0.f, 0.f);
+    __syncwarp();
+  }
+  if (valid && w == 0) {
     const unsigned full = 0xffffffffu;
-    const int p0 = (np * w) / nw, p1 = (np * (w + 1)) / nw;
+    const int p0 = 0, p1 = np;
     for (int c0 = p0; c0 < p1; c0 += 32) {
       const int i = c0 + l32;
       const bool act = i < p1;
@@ -1042,8 +1025,34 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
       }
     }
   }
-  __syncthreads();  // every warp's grid complete
+  __syncthreads();  // the grid is complete
   return mirror;
+}
+
+// The adjoint row kernel with the pair spread (spread mode 3), a kernel of its
+// own so that its register allocation does not carry the other schemes.
+template <int H, bool ZF>
+__global__ void __launch_bounds__(1024) row_adjoint_pairs_kernel(RowLaunch L, WindowPoly W) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_item;
+  float4* nodes_all = reinterpret_cast<float4*>(smem + L.fft_region);
+  for (;;) {
+    const int item = next_item(L.counter, &s_item);
+    if (item >= L.nitems) break;
+    const WorkItem wi = L.items[item];
+    const RowProblem& P = L.problems[wi.problem];
+    const int tpr = P.tpr, M = P.M, nt = P.nt;
+    const int slot = threadIdx.x / tpr;
+    const int lane = threadIdx.x - slot * tpr;
+    const int row = wi.row0 + slot;
+    const bool valid = row < P.rows;
+    float2* X = smem + slot * P.slot;
+    float4* N = nodes_all + slot * (P.nz + 2);
+    const bool mirror = adjoint_pairs<H, ZF>(P, W, row, valid, lane, X, N);
+    const float scale = (valid && !ZF && mirror) ? 0.5f : 1.0f;
+    float2* dst = const_cast<float2*>(P.pt) + (size_t)(valid ? row : 0) * nt;
+    fft_inverse_crop(X, M, P.mshift, nt, lane, tpr, L.tw, L.Mmax >> P.mshift, dst, P.prescale, scale, valid);
+  }
 }
 
 // ZF = false: input is the half image spectrum (image R2C over all axes) with
@@ -1066,14 +1075,6 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
     const bool valid = row < P.rows;
     float2* X = smem + slot * P.slot;
     float4* N = nodes_all + slot * (P.nz + 2);
-    if (L.spread_mode == 3) {
-      float2* X2 = tpr >= 64 ? smem + L.grid2_off + slot * P.slot : nullptr;
-      const bool mirror = adjoint_pairs<H, ZF>(P, W, row, valid, lane, X, X2, N);
-      const float scale = (valid && !ZF && mirror) ? 0.5f : 1.0f;
-      float2* dst = const_cast<float2*>(P.pt) + (size_t)(valid ? row : 0) * nt;
-      fft_inverse_crop(X, M, P.mshift, nt, lane, tpr, L.tw, L.Mmax >> P.mshift, dst, P.prescale, scale, valid, X2);
-      continue;
-    }
     const int nzh = P.nz >> 1;
     RowGeom rg;
     int nneg = 1, nn = 0;

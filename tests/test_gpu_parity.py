@@ -461,8 +461,8 @@ def test_deterministic_spread(pai, g):
 def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
     """Every spread, forced with PAI_SPREAD (the tuner may prefer any), for the
     adjoint against the oracle's adjoint, and the forward model against its
-    oracle.  "pairs" (node pairs into warp-private grids) applies to rows of one
-    warp (padded length 512: 2d) or two warps (1024: the m1024 cases); the
+    oracle.  "pairs" (node pairs spread by one warp per row) applies to rows of
+    one warp (padded length 512: 2d) or two warps (1024: the m1024 cases); the
     others fall back to the tap phases."""
     import oracle.methods as om
     monkeypatch.setenv("PAI_SPREAD", mode)
@@ -487,7 +487,7 @@ def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
 @pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
                                ph.Geometry(dim=3, nx=24, ny=20, nt=512, nz=96, dz=0.7)], ids=["m512", "m1024"])
 def test_pair_spread_repeats_bit_for_bit(pai, g, monkeypatch):
-    """The pair spread sums every grid cell in a fixed order (warp-private grids,
+    """The pair spread sums every grid cell in a fixed order (one warp per row,
     plain read-modify-writes separated by warp barriers): two calls give
     identical bits, and it agrees with the atomic spread to FP32 rounding."""
     import torch
@@ -530,3 +530,44 @@ def test_window_tuner_on_a_batch(pai):
         n = g.nx * g.nz
         assert rel(out[off: off + n].reshape(g.image_shape), oracle.reconstruct(g, p.astype(np.float64))) < TOL
         off += n
+
+
+def test_pair_spread_on_a_mixed_batch(pai, monkeypatch):
+    """The pair spread in one batched launch over problems whose rows take one
+    warp (padded length 512) and two warps (1024), 2-D and 3-D, against the
+    oracle's adjoint problem by problem, and bit-repeatable."""
+    import torch
+    monkeypatch.setenv("PAI_SPREAD", "pairs")
+    geoms = [ph.Geometry(dim=2, nx=40, nt=200, nz=80, dz=0.9),
+             ph.Geometry(dim=2, nx=24, nt=400, nz=120, c=1.2),
+             ph.Geometry(dim=3, nx=10, ny=8, nt=256, nz=48, dy=1.1),
+             ph.Geometry(dim=3, nx=8, ny=6, nt=480, nz=64)]
+    plan = pai.Plan([gdict(g, K=3) for g in geoms])
+    assert sorted({plan.problem_info(i)["M"] for i in range(4)}) == [512, 1024]
+    hs = [np.asarray(ph.random_image(500 + i, g), np.float32) for i, g in enumerate(geoms)]
+    h = to_gpu(np.concatenate([x.ravel() for x in hs]))
+    a = plan.adjoint(h).clone()
+    assert torch.equal(a, plan.adjoint(h))
+    got = to_np(a)
+    off = 0
+    for g, x in zip(geoms, hs):
+        n = g.nx * g.ny * g.nt
+        assert rel(got[off: off + n].reshape(g.data_shape), oracle.adjoint(g, x.astype(np.float64))) < TOL, g
+        off += n
+
+
+def test_plans_of_the_same_geometries_reuse_the_tuning(pai, monkeypatch):
+    """A second plan of the same geometries on the same device takes the first
+    plan's tuned choices (window, CTA sizes, spread, pipelines) instead of
+    timing again, so both give the same bits; PAI_WISDOM=0 tunes afresh."""
+    import torch
+    geoms = [ph.Geometry(dim=2, nx=48, nt=4 * k, nz=2 * k) for k in (37, 53, 90)]
+    a = pai.Plan([gdict(g) for g in geoms])
+    b = pai.Plan([gdict(g) for g in geoms])
+    assert b.tuning_log.startswith("reused")
+    assert [a.problem_info(i) for i in range(3)] == [b.problem_info(i) for i in range(3)]
+    p = to_gpu(np.concatenate([ph.random_data(600 + i, g).ravel() for i, g in enumerate(geoms)]))
+    assert torch.equal(a.reconstruct(p), b.reconstruct(p))
+    monkeypatch.setenv("PAI_WISDOM", "0")
+    c = pai.Plan([gdict(g) for g in geoms])
+    assert not c.tuning_log.startswith("reused") and "window: kept" in c.tuning_log
