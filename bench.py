@@ -92,7 +92,7 @@ def workload(name: str, seed: int = 0):
     if name == "batched2d":
         probs = ph.batched_2d(seed)
         return ("64 uneven 2-D problems (nx = 2 U{128..1024}, nt = 2 U{256..2048}, nz = nt/2) in one plan; "
-                "f_circ disc phantoms; window chosen by the planner (truncation error <= 1e-8)",
+                "f_circ disc phantoms; window left open: chosen by the plan's window tuner (truncation error <= 1e-7)",
                 [gd(p.geom) for p in probs], [p.p.astype(np.float32) for p in probs])
     raise SystemExit(f"unknown config {name}")
 
@@ -472,6 +472,7 @@ def run_forward_model(args, rank, world, local_rank):
                                                            "lateral_inverse_fft": st[2]}},
             "cpu_baseline": None, "e2e": {"value": None, "unit": UNIT, "note": "no host-memory entry point"},
             "gpu_launches": launches, "clocks": clocks, "wall_s_timed_region": t1 - t0,
+            "tuning_log": model.tuning_log.strip().splitlines(),
         }))
     model.close()
 

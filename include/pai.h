@@ -210,19 +210,28 @@ pai_status pai_profile_stages(pai_plan_t plan, const float* d_in, float* d_out, 
 pai_status pai_set_stream(pai_plan_t plan, void* cuda_stream);
 
 /* Spread of pai_adjoint and pai_forward_model (the transpose of the window
- * gather, Algorithm 1 read backwards).  Three spreads exist: shared-memory
- * atomic adds per node (every node adds its 2H tap contributions to the
- * oversampled grid at once), the same per run (the first node of each run of
- * nodes on the same grid cell sums the run and adds once per tap) -- for both
- * the order of the additions into one grid cell, hence the last bits of the
- * result, may differ from call to call -- and tap phases (nodes add tap by
- * tap in a fixed order, one barrier per phase; bit-identical on repeated
- * calls).  pai_plan times all three and keeps the fastest (the environment
- * variable PAI_SPREAD=atomic, =runs or =tap forces one).
- * deterministic = 1: use the tap phases; deterministic = 0: back to the
- * plan's choice.  pai_reconstruct is deterministic either way.  Waits for the
- * plan's stream and drops the plan's captured CUDA graphs (they are captured
- * again on next use).  Any other value: PAI_ERR_INVALID_ARG.               */
+ * gather, Algorithm 1 read backwards).  Five spreads exist:
+ *   atomic        shared-memory atomic adds per node (every node adds its 2H
+ *                 tap contributions to the oversampled grid at once);
+ *   runs          the same per run (the first node of each run of nodes on
+ *                 the same grid cell sums the run and adds once per tap);
+ *   tap           tap phases (nodes add tap by tap in a fixed order, one
+ *                 barrier per phase);
+ *   pairs         the nodes +-nu of a row as pairs, spread by one warp per row
+ *                 (32 pairs at a time, runs summed by warp shuffles, plain
+ *                 read-modify-writes; windowed methods, rows of 32 or 64
+ *                 threads);
+ *   pairs_atomic  the same by every warp of the row, adding with shared-memory
+ *                 atomics (windowed methods).
+ * tap and pairs are bit-identical on repeated calls; for the three atomic
+ * spreads the order of the additions into one grid cell, hence the last bits
+ * of the result, may differ from call to call.  pai_plan times every spread
+ * that applies and keeps the fastest (the environment variable PAI_SPREAD
+ * forces one by the names above).
+ * deterministic = 1: the faster of tap and pairs; deterministic = 0: back to
+ * the plan's choice.  pai_reconstruct is deterministic either way.  Waits for
+ * the plan's stream and drops the plan's captured CUDA graphs (they are
+ * captured again on next use).  Any other value: PAI_ERR_INVALID_ARG.      */
 pai_status pai_set_deterministic(pai_plan_t plan, int deterministic);
 
 /* Fill *info with the plan's parameters (M, oversampling, K and alpha of

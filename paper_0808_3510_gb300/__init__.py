@@ -403,8 +403,8 @@ class Plan:
         return [ms[0], ms[1], ms[2]]
 
     def set_deterministic(self, on: bool = True):
-        """Bit-identical adjoints on repeated calls (tap-phased spread) instead of the
-        faster shared-memory atomic spread (``pai_set_deterministic``).  Plans made
+        """Bit-identical adjoints on repeated calls (tap-phased or node-pair spread) instead
+        of a faster spread that adds with shared-memory atomics (``pai_set_deterministic``).  Plans made
         while ``torch.use_deterministic_algorithms(True)`` is on start deterministic."""
         _check(self._lib.pai_set_deterministic(self._h, 1 if on else 0), "pai_set_deterministic")
 
@@ -439,11 +439,7 @@ class Plan:
     @property
     def tuning_log(self) -> str:
         """What the tuner timed and kept when the plan was built (``pai_tuning_log``)."""
-        n = ctypes.c_size_t()
-        _check(self._lib.pai_tuning_log(self._h, None, 0, ctypes.byref(n)), "pai_tuning_log")
-        buf = ctypes.create_string_buffer(n.value + 1)
-        _check(self._lib.pai_tuning_log(self._h, buf, n.value + 1, None), "pai_tuning_log")
-        return buf.value.decode()
+        return _tuning_log(self._lib, self._h)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -455,6 +451,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _tuning_log(lib, h) -> str:
+    n = ctypes.c_size_t()
+    _check(lib.pai_tuning_log(h, None, 0, ctypes.byref(n)), "pai_tuning_log")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib.pai_tuning_log(h, buf, n.value + 1, None), "pai_tuning_log")
+    return buf.value.decode()
 
 
 class ForwardModel:
@@ -526,6 +530,11 @@ class ForwardModel:
         n = ctypes.c_longlong()
         _check(self._lib.pai_launch_count(self._h, ctypes.byref(n)), "pai_launch_count")
         return n.value
+
+    @property
+    def tuning_log(self) -> str:
+        """What the box plan's tuner timed and kept (``pai_tuning_log``): the spread."""
+        return _tuning_log(self._lib, self._h)
 
     def profile_stages(self, reps: int = 10):
         """Mean device ms of (image-side transforms, forward-model row kernel, lateral inverse) on the box."""

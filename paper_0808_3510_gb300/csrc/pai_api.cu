@@ -74,6 +74,8 @@ struct pai_plan_s {
   bool pairs_ok = false;                            // spread mode 3 applies to every problem of the plan
   size_t smem_adj3 = 0;                             // mode 3: shared memory of the adjoint row kernel
   int ctas_adj3 = 0;                                //         and its CTA count
+  bool pairs_atom_ok = false;                       // spread mode 4 applies to every problem of the plan
+  int ctas_adj4 = 0;                                // mode 4: CTA count (shared memory as mode 3)
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
   bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
@@ -336,10 +338,10 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
 pai_status enqueue_row(pai_plan_s* P, bool adjoint, cudaStream_t s, int threads, int ctas, size_t smem,
                        bool zf = false) {
   RowLaunch L = make_launch(P, adjoint);
-  if (adjoint && P->spread_mode == 3) {
-    // the pair-spread kernel's own occupancy gives its CTA count
+  if (adjoint && (P->spread_mode == 3 || P->spread_mode == 4)) {
+    // the pair-spread kernels' own occupancy gives their CTA counts
     smem = P->smem_adj3;
-    ctas = P->ctas_adj3;
+    ctas = P->spread_mode == 3 ? P->ctas_adj3 : P->ctas_adj4;
   }
   PAI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(int), s));
   cudaError_t e = adjoint ? launch_row_adjoint(L, P->poly, threads, ctas, smem, s, zf)
@@ -920,24 +922,35 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     // methods, rows of one or two warps, and 32 consecutive pairs spanning
     // fewer than M - 2H cells (consecutive nodes of one sign are at most
     // M c dt / (nz dz) cells apart)
+    // spread mode 4 (every warp of the row, atomics): windowed methods and
+    // rows of whole warps
     P->pairs_ok = !method_interp(P->method) && std::getenv("PAI_NO_PAIRS") == nullptr;
+    P->pairs_atom_ok = P->pairs_ok;
     for (auto& p : P->probs) {
       const double g1 = std::ceil((double)p.M * p.g.c * p.g.dt / (p.g.nz * p.g.dz)) + 1.0;
       if (p.tpr != 32 && p.tpr != 64) P->pairs_ok = false;
       if (!(32.0 * g1 + 2.0 * P->H + 2.0 < (double)p.M)) P->pairs_ok = false;
+      if (p.tpr % 32 != 0) P->pairs_atom_ok = false;
     }
     P->smem_adj3 = P->smem_adj;
     P->ctas_adj3 = 0;
+    P->ctas_adj4 = 0;
     if (P->pairs_ok) {
       const int occ3 = row_kernel_max_ctas_per_sm(2, T, P->smem_adj3, P->H, P->zf);
       if (occ3 < 1) P->pairs_ok = false;
       P->ctas_adj3 = occ3 * sms;
+    }
+    if (P->pairs_atom_ok) {
+      const int occ4 = row_kernel_max_ctas_per_sm(4, T, P->smem_adj3, P->H, P->zf);
+      if (occ4 < 1) P->pairs_atom_ok = false;
+      P->ctas_adj4 = occ4 * sms;
     }
     std::vector<WorkItem> items;
     build_items(T, items);
     P->nitems_adj = (int)items.size();
     P->ctas_adj = std::min(P->nitems_adj, occ_a * sms);
     P->ctas_adj3 = std::min(P->nitems_adj, P->ctas_adj3);
+    P->ctas_adj4 = std::min(P->nitems_adj, P->ctas_adj4);
     if (P->d_items_adj == P->d_items_fwd) P->d_items_adj = nullptr;
     if (P->d_items_adj) P->alloc_used -= (long long)P->items_adj_bytes;
     cudaFree(P->d_items_adj);
@@ -1047,7 +1060,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_pt, 0, pt_off * sizeof(float2)));
-    for (int T : {64, 128, 256, 512, 1024}) {
+    for (int T : {32, 64, 128, 256, 512, 1024}) {
       if (T < tpr_max) continue;
       if (finish_shape(T) != PAI_OK) continue;
       float best = 1e30f;
@@ -1087,7 +1100,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
-    for (int T : {64, 128, 256, 512, 1024}) {
+    for (int T : {32, 64, 128, 256, 512, 1024}) {
       if (T < tpr_max) continue;
       if (finish_shape_adj(T) != PAI_OK) continue;
       float best = 1e30f;
@@ -1121,22 +1134,27 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
                  : std::strcmp(env_spread, "tap") == 0 ? 0
                  : std::strcmp(env_spread, "atomic") == 0 ? 1
                  : std::strcmp(env_spread, "runs") == 0 ? 2
-                 : std::strcmp(env_spread, "pairs") == 0 ? 3 : -1;
+                 : std::strcmp(env_spread, "pairs") == 0 ? 3
+                 : std::strcmp(env_spread, "pairs_atomic") == 0 ? 4 : -1;
   if (env_mode == 3 && !P->pairs_ok) env_mode = 0;
+  if (env_mode == 4 && !P->pairs_atom_ok) env_mode = 1;
   P->spread_det = P->pairs_ok ? 3 : 0;
   if (env_mode >= 0) {
     P->spread_tuned = env_mode;
   } else if (have_wis) {
-    P->spread_tuned = wis.spread_tuned == 3 && !P->pairs_ok ? 0 : wis.spread_tuned;
+    P->spread_tuned = wis.spread_tuned == 3 && !P->pairs_ok         ? 0
+                      : wis.spread_tuned == 4 && !P->pairs_atom_ok ? 1
+                                                                   : wis.spread_tuned;
     P->spread_det = wis.spread_det == 3 && !P->pairs_ok ? 0 : wis.spread_det;
   } else if (tune || qmode) {
     cudaEvent_t e0, e1;
     PAI_CUDA(cudaEventCreate(&e0));
     PAI_CUDA(cudaEventCreate(&e1));
     PAI_CUDA(cudaMemset(P->d_fh, 0, fh_off * sizeof(float2)));
-    float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
-    for (int mode = 0; mode < 4; ++mode) {
+    float best_ms[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    for (int mode = 0; mode < 5; ++mode) {
       if (mode == 3 && !P->pairs_ok) continue;
+      if (mode == 4 && !P->pairs_atom_ok) continue;
       P->spread_mode = mode;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, P->cap_stream);
@@ -1151,15 +1169,16 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
-    static const char* kSpreadName[4] = {"tap phases", "atomics per node", "atomics per run", "node pairs"};
-    for (int mode = 0; mode < 4; ++mode)
+    static const char* kSpreadName[5] = {"tap phases", "atomics per node", "atomics per run", "node pairs",
+                                         "node pairs, atomics"};
+    for (int mode = 0; mode < 5; ++mode)
       if (best_ms[mode] < 1e29f) {
         std::snprintf(logline, sizeof logline, "adjoint spread: %s: adjoint row kernel %.4f ms\n", kSpreadName[mode],
                       best_ms[mode]);
         P->tune_log += logline;
       }
     P->spread_tuned = 0;
-    for (int mode = 1; mode < 4; ++mode)
+    for (int mode = 1; mode < 5; ++mode)
       if (best_ms[mode] < best_ms[P->spread_tuned]) P->spread_tuned = mode;
     P->spread_det = (P->pairs_ok && best_ms[3] < best_ms[0]) ? 3 : 0;
   }

@@ -92,7 +92,8 @@ struct RowLaunch {
   int spread_mode;             // adjoint spread: 0 tap phases (deterministic), 1 shared-memory atomics per
                                // node, 2 shared-memory atomics per run of nodes with equal j0, 3 node pairs
                                // spread by one warp per row (deterministic; windowed methods, 32 or 64
-                               // threads per row)
+                               // threads per row), 4 node pairs spread by every warp of the row with
+                               // shared-memory atomics (windowed methods, a multiple of 32 threads per row)
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)
@@ -174,7 +175,8 @@ cudaError_t launch_lateral_c2c(const float2* in, float2* out, int L, int C, int 
 // In-place FFT of `rows` contiguous complex lines of power-of-two length L (32 <= L <= 16384).
 cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const float2* tw, int twstride,
                             cudaStream_t s);
-// kind: 0 forward row kernel, 1 adjoint row kernel, 2 adjoint row kernel with the pair spread
+// kind: 0 forward row kernel, 1 adjoint row kernel, 2 adjoint row kernel with the pair spread, 4 with the
+// atomic pair spread
 int row_kernel_max_ctas_per_sm(int kind, int threads, size_t smem, int H, bool zf = false);
 
 // Data cutoff w_cut (pai_cutoff.cu).  R = ceil(sqrt(eps)); the table holds

@@ -41,18 +41,24 @@ template <int H>
 static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem, cudaStream_t s,
                          bool zf) {
   if (L.spread_mode == 3)
-    return zf ? launch_k(row_adjoint_pairs_kernel<H, true>, L, w, threads, ctas, smem, s)
-              : launch_k(row_adjoint_pairs_kernel<H, false>, L, w, threads, ctas, smem, s);
+    return zf ? launch_k(row_adjoint_pairs_kernel<H, true, false>, L, w, threads, ctas, smem, s)
+              : launch_k(row_adjoint_pairs_kernel<H, false, false>, L, w, threads, ctas, smem, s);
+  if (L.spread_mode == 4)
+    return zf ? launch_k(row_adjoint_pairs_kernel<H, true, true>, L, w, threads, ctas, smem, s)
+              : launch_k(row_adjoint_pairs_kernel<H, false, true>, L, w, threads, ctas, smem, s);
   return zf ? launch_k(row_adjoint_kernel<H, true>, L, w, threads, ctas, smem, s)
             : launch_k(row_adjoint_kernel<H, false>, L, w, threads, ctas, smem, s);
 }
 
-// kind: 0 forward, 1 adjoint, 2 adjoint with the pair spread
+// kind: 0 forward, 1 adjoint, 2 adjoint with the pair spread, 4 with the atomic pair spread
 template <int H>
 static int occ_h(int kind, int threads, size_t smem, bool zf) {
   if (kind == 2)
-    return zf ? occ_k(row_adjoint_pairs_kernel<H, true>, threads, smem)
-              : occ_k(row_adjoint_pairs_kernel<H, false>, threads, smem);
+    return zf ? occ_k(row_adjoint_pairs_kernel<H, true, false>, threads, smem)
+              : occ_k(row_adjoint_pairs_kernel<H, false, false>, threads, smem);
+  if (kind == 4)
+    return zf ? occ_k(row_adjoint_pairs_kernel<H, true, true>, threads, smem)
+              : occ_k(row_adjoint_pairs_kernel<H, false, true>, threads, smem);
   if (kind == 1)
     return zf ? occ_k(row_adjoint_kernel<H, true>, threads, smem) : occ_k(row_adjoint_kernel<H, false>, threads, smem);
   return zf ? occ_k(row_forward_kernel<H, true>, threads, smem) : occ_k(row_forward_kernel<H, false>, threads, smem);

@@ -871,7 +871,10 @@ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
 // separates the steps.  Every cell therefore receives its terms in a fixed
 // order: the result is bit-repeatable.
 // Returns whether the row is a mirror row (non-ZF input, both destinations).
-template <int H, bool ZF>
+// ATOM (spread mode 4, rows of any number of warps): every warp of the slot
+// spreads its share of the 32-pair chunks, each run's sum added with
+// shared-memory atomics (the order of the additions into a cell varies).
+template <int H, bool ZF, bool ATOM = false>
 __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowPoly& W, int row, bool valid, int lane,
                                               float2* X, float4* A) {
   const int tpr = P.tpr, M = P.M, nt = P.nt, mask = M - 1;
@@ -962,14 +965,18 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
   // 64 threads) waits at the barrier below
   const int w = lane >> 5, l32 = lane & 31;
   float2* G = X;
-  if (w == 0) {
+  if (ATOM) {
+    for (int g = lane; g < M; g += tpr) G[PADI(g)] = make_float2(0.f, 0.f);
+    __syncthreads();  // the grid is zero before any warp adds to it
+  } else if (w == 0) {
     for (int g = l32; g < M; g += 32) G[PADI(g)] = make_float2(0.f, 0.f);
     __syncwarp();
   }
-  if (valid && w == 0) {
+  if (valid && (ATOM || w == 0)) {
     const unsigned full = 0xffffffffu;
-    const int p0 = 0, p1 = np;
-    for (int c0 = p0; c0 < p1; c0 += 32) {
+    const int p1 = np;
+    const int c_first = ATOM ? 32 * w : 0, c_step = ATOM ? tpr : 32;
+    for (int c0 = c_first; c0 < p1; c0 += c_step) {
       const int i = c0 + l32;
       const bool act = i < p1;
       const float4 a = act ? A[i] : make_float4(0.f, 0.5f, 0.f, 0.f);
@@ -1018,9 +1025,14 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
         for (int k = 0; k < 4; ++k) {
           if (head) {
             float2* q = G + PADI(cell[k] & mask);
-            *q = cadd(*q, c[k]);
+            if (ATOM) {
+              atomicAdd(&q->x, c[k].x);
+              atomicAdd(&q->y, c[k].y);
+            } else {
+              *q = cadd(*q, c[k]);
+            }
           }
-          __syncwarp();
+          if (!ATOM) __syncwarp();
         }
       }
     }
@@ -1031,7 +1043,7 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
 
 // The adjoint row kernel with the pair spread (spread mode 3), a kernel of its
 // own so that its register allocation does not carry the other schemes.
-template <int H, bool ZF>
+template <int H, bool ZF, bool ATOM>
 __global__ void __launch_bounds__(1024) row_adjoint_pairs_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
@@ -1048,7 +1060,7 @@ __global__ void __launch_bounds__(1024) row_adjoint_pairs_kernel(RowLaunch L, Wi
     const bool valid = row < P.rows;
     float2* X = smem + slot * P.slot;
     float4* N = nodes_all + slot * (P.nz + 2);
-    const bool mirror = adjoint_pairs<H, ZF>(P, W, row, valid, lane, X, N);
+    const bool mirror = adjoint_pairs<H, ZF, ATOM>(P, W, row, valid, lane, X, N);
     const float scale = (valid && !ZF && mirror) ? 0.5f : 1.0f;
     float2* dst = const_cast<float2*>(P.pt) + (size_t)(valid ? row : 0) * nt;
     fft_inverse_crop(X, M, P.mshift, nt, lane, tpr, L.tw, L.Mmax >> P.mshift, dst, P.prescale, scale, valid);

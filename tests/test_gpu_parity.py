@@ -451,7 +451,7 @@ def test_deterministic_spread(pai, g):
         torch.use_deterministic_algorithms(prev)
 
 
-@pytest.mark.parametrize("mode", ["atomic", "runs", "tap", "pairs"])
+@pytest.mark.parametrize("mode", ["atomic", "runs", "tap", "pairs", "pairs_atomic"])
 @pytest.mark.parametrize("g,method", [(ph.Geometry(dim=2, nx=96, nt=200, nz=80, dz=0.9), "kb"),
                                       (ph.Geometry(dim=3, nx=20, ny=16, nt=48, nz=24, dy=1.2), "kb"),
                                       (ph.Geometry(dim=2, nx=64, nt=128, nz=64), "linear"),
@@ -463,7 +463,8 @@ def test_spread_modes_against_oracle(pai, g, method, mode, monkeypatch):
     adjoint against the oracle's adjoint, and the forward model against its
     oracle.  "pairs" (node pairs spread by one warp per row) applies to rows of
     one warp (padded length 512: 2d) or two warps (1024: the m1024 cases); the
-    others fall back to the tap phases."""
+    others fall back to the tap phases.  "pairs_atomic" applies to every
+    windowed case (the linear one falls back to the atomic spread)."""
     import oracle.methods as om
     monkeypatch.setenv("PAI_SPREAD", mode)
     plan = pai.Plan(gdict(g, method=method, oversampling=2.0))
@@ -499,6 +500,30 @@ def test_pair_spread_repeats_bit_for_bit(pai, g, monkeypatch):
     monkeypatch.setenv("PAI_SPREAD", "atomic")
     ref = pai.Plan(gdict(g, K=3)).adjoint(h)
     assert rel(to_np(a), to_np(ref)) < 1e-6
+
+
+@pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=48, nt=2000, nz=700, dz=1.3, c=1.1),
+                               ph.Geometry(dim=3, nx=6, ny=4, nt=1800, nz=256, dx=1.2)], ids=["2d-m4096", "3d-m4096"])
+def test_atomic_pair_spread_on_long_rows(pai, g, monkeypatch):
+    """The atomic node-pair spread on rows of many warps (padded length 4096,
+    256 threads per row) against the oracle's adjoint."""
+    monkeypatch.setenv("PAI_SPREAD", "pairs_atomic")
+    plan = pai.Plan(gdict(g, K=3))
+    assert plan.problem_info(0)["M"] == 4096
+    h = np.asarray(ph.random_image(34, g), np.float32)
+    assert rel(to_np(plan.adjoint(to_gpu(h))), oracle.adjoint(g, h.astype(np.float64))) < TOL
+
+
+@pytest.mark.parametrize("g", [ph.Geometry(dim=2, nx=8, nt=1000, nz=12, c=0.1),
+                               ph.Geometry(dim=2, nx=16, nt=2000, nz=24, c=0.05, dz=0.8)], ids=["m2048", "m4096"])
+def test_atomic_pair_spread_forward_model(pai, g, monkeypatch):
+    """The forward model with the atomic node-pair spread on rows of 128 and 256
+    threads (a slow wave speed keeps the periodic box small and puts many nodes
+    on one grid cell), against the oracle's direct sums."""
+    monkeypatch.setenv("PAI_SPREAD", "pairs_atomic")
+    model = pai.ForwardModel(gdict(g, K=3))
+    f = np.asarray(ph.random_image(35, g), np.float32)
+    assert rel(to_np(model(to_gpu(f))), oracle.forward_model(g, f.astype(np.float64))) < TOL
 
 
 def test_window_tuner_on_a_batch(pai):
