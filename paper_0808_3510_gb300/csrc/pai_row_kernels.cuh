@@ -90,6 +90,24 @@ __host__ __device__ constexpr float sin16(int q) {
        : q == 6 ? 0.70710678118654752f : 0.38268343236508977f;
 }
 
+// cos and sin of 2 pi q / 32, q = 0..8
+__host__ __device__ constexpr float cos32(int q) {
+  return q == 0 ? 1.0f : q == 1 ? 0.98078528040323044913f : q == 2 ? 0.92387953251128675613f
+       : q == 3 ? 0.83146961230254523708f : q == 4 ? 0.70710678118654752440f : q == 5 ? 0.55557023301960222474f
+       : q == 6 ? 0.38268343236508977173f : q == 7 ? 0.19509032201612826785f : 0.0f;
+}
+__host__ __device__ constexpr float sin32(int q) { return cos32(8 - q); }
+
+// x * e^{-+ 2 pi i q / 32}, q = 0..8  (CONJ: plus sign)
+template <int Q, bool CONJ>
+__device__ __forceinline__ float2 tw32(float2 x) {
+  if (Q == 0) return x;
+  if (Q == 8) return CONJ ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+  constexpr float c = cos32(Q);
+  constexpr float s = CONJ ? sin32(Q) : -sin32(Q);
+  return fma2(make_float2(x.x, x.x), make_float2(c, s), mul2(make_float2(x.y, x.y), make_float2(-s, c)));
+}
+
 // x * e^{-+ 2 pi i q / 16}  (forward: minus sign; INV: plus sign)
 template <int Q, bool INV>
 __device__ __forceinline__ float2 twq(float2 x) {
@@ -189,6 +207,24 @@ __device__ __forceinline__ void tw_load(TwBase<R>& t, const float2* __restrict__
   if (R >= 16) t.b[3] = tw_at(tw, 8 * step);
 }
 
+// x * e^{-2 pi i q / 16}, q = 0..15 (a constant once the caller's loop is unrolled)
+__device__ __forceinline__ float2 rot16(float2 x, int q) {
+  const float c = (q & 8) ? -cos16(q & 7) : cos16(q & 7);
+  const float s = (q & 8) ? sin16(q & 7) : -sin16(q & 7);
+  return fma2(make_float2(x.x, x.x), make_float2(c, s), mul2(make_float2(x.y, x.y), make_float2(-s, c)));
+}
+
+// Base twiddles of butterfly j + i M/16 from those of butterfly j, for the last
+// pass of a transform (Ns R = M, so the twiddle index is the butterfly index):
+// w^{2^e (j + i M/16)} = w^{2^e j} e^{-2 pi i (2^e i mod 16) / 16}.
+template <int R>
+__device__ __forceinline__ void tw_shift(TwBase<R>& t, const TwBase<R>& t0, int i) {
+  t.b[0] = rot16(t0.b[0], i & 15);
+  if (R >= 4) t.b[1] = rot16(t0.b[1], (2 * i) & 15);
+  if (R >= 8) t.b[2] = rot16(t0.b[2], (4 * i) & 15);
+  if (R >= 16) t.b[3] = rot16(t0.b[3], (8 * i) & 15);
+}
+
 template <bool INV>
 __device__ __forceinline__ float2 twc(float2 w) {
   return INV ? make_float2(w.x, -w.y) : w;
@@ -240,6 +276,10 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
   TwBase<R> t[NB];
   const int MR = M / R;
   const int tws = (M / (Ns * R)) * twstride;
+  // A last pass of radix < 16 (several butterflies per thread, at j = lane +
+  // i M/16): their twiddles follow from the first butterfly's by constant
+  // rotations (tw_shift) instead of table loads.
+  const bool chain = NB > 1 && Ns > 1 && Ns * R == M && tpr * kElemsPerThread == M;
   // twiddles do not depend on the data: for radix 16 (one butterfly per
   // thread) their loads are issued before the barrier; smaller radices carry
   // several butterflies per thread and load after it to stay within registers
@@ -269,7 +309,10 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
     const int j = lane + i * tpr;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      if (NB != 1) tw_load<R>(t[i], tw, k * tws);
+      if (NB != 1) {
+        if (!chain || i == 0) tw_load<R>(t[i], tw, k * tws);
+        else tw_shift<R>(t[i], t[0], i);
+      }
       tw_apply<R, INV>(v[i], t[i]);
     }
     dft_reg<R, INV>(v[i]);
@@ -367,13 +410,66 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
   __syncthreads();
 }
 
-// Remaining passes after a first radix-16 pass (Ns = 16 on entry); the last
-// pass writes layout OUT.
+// First forward pass of radix 32 at oversampling 2 when M = 32 16^k: the
+// transform then takes radix-16 passes only (no radix-2 pass at its end).
+// Butterfly j (0 <= j < M/32) has inputs x_r at positions j + r M/32, which
+// hold samples for r = 0..7 and r = 24..31 only (the rest is padding), and
+// outputs X[32 j + q].  Two threads share it: h = 0 computes the even outputs
+// X[32 j + 2m] = sum_s z_s w16^{sm} with z_s = x_s + x_{s+16}, h = 1 the odd
+// ones with z_s = (x_s - x_{s+16}) w32^s, w_N = e^{-2 pi i/N}; of each pair
+// x_s, x_{s+16} one is padding (s < 8: x_{s+16}; s >= 8: x_s).  Both threads
+// load the butterfly's 16 samples.  Writes padded: PADI(32 j + q) = 33 j + q.
+__device__ __forceinline__ void fft_first_pass32_from_global(float2* X, int M, int nt, int lane, int tpr,
+                                                             const float2* __restrict__ src,
+                                                             const float* __restrict__ prescale) {
+  const int half = tpr >> 1, q4 = M >> 2, M32 = M >> 5;
+  const int h = lane >= half ? 1 : 0;
+  const int j = lane - h * half;
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int n = s < 8 ? j + s * M32 + q4 : j + (s - 8) * M32;
+    const float2 g = __ldg(&src[n]);
+    const float p = __ldg(&prescale[n]);
+    v[s] = make_float2(p * g.x, p * g.y);
+  }
+  if (h) {
+    v[1] = tw32<1, false>(v[1]);
+    v[2] = tw32<2, false>(v[2]);
+    v[3] = tw32<3, false>(v[3]);
+    v[4] = tw32<4, false>(v[4]);
+    v[5] = tw32<5, false>(v[5]);
+    v[6] = tw32<6, false>(v[6]);
+    v[7] = tw32<7, false>(v[7]);
+    // s >= 8: -w32^s = conj(w32^{16-s})
+    v[8] = tw32<8, true>(v[8]);
+    v[9] = tw32<7, true>(v[9]);
+    v[10] = tw32<6, true>(v[10]);
+    v[11] = tw32<5, true>(v[11]);
+    v[12] = tw32<4, true>(v[12]);
+    v[13] = tw32<3, true>(v[13]);
+    v[14] = tw32<2, true>(v[14]);
+    v[15] = tw32<1, true>(v[15]);
+  }
+  dft_reg<16, false>(v);
+  float2* dst = X + 33 * j + h;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) dst[2 * m] = v[m];
+  __syncthreads();
+}
+
+// Whether the forward transform of a row starts with the radix-32 pass.
+__device__ __forceinline__ bool first_pass32(int M, int mshift, int nt) {
+  return M == 2 * nt && mshift >= 9 && ((mshift - 5) & 3) == 0;
+}
+
+// Remaining passes after a first pass of radix 2^ns_shift (16 or 32: Ns on
+// entry); the last pass writes layout OUT.
 template <bool INV, int OUT>
 __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
-                                         int twstride, bool active = true) {
-  int Ns = 16;
-  int rem = mshift - 4;
+                                         int twstride, bool active = true, int ns_shift = 4) {
+  int Ns = 1 << ns_shift;
+  int rem = mshift - ns_shift;
   while (rem >= 4) {
     if (rem == 4) {
       fft_pass<16, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
@@ -812,8 +908,11 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     const bool valid = row < P.rows;
     float2* X = smem + slot * P.slot;
     // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
-    fft_first_pass_from_global(X, M, P.nt, lane, tpr, P.pt + (size_t)(valid ? row : 0) * P.nt, P.prescale);
-    fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift);
+    const float2* src = P.pt + (size_t)(valid ? row : 0) * P.nt;
+    const bool r32 = first_pass32(M, P.mshift, P.nt);
+    if (r32) fft_first_pass32_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
+    else fft_first_pass_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
+    fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift, true, r32 ? 5 : 4);
     if (valid) {
       if (!ZF) gather_row<H>(P, W, X, row, lane);
       else gather_row_z<H>(P, W, X, P.fh + (size_t)row * P.nz, row, lane);
