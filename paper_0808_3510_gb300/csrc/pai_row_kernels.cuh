@@ -583,7 +583,7 @@ __device__ __forceinline__ void fft_smem(float2* X, int M, int mshift, int lane,
 // Returns j0 = floor(x), fr = x - j0 in [0,1), and x0 = FP32 value of x.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void node_position(float2 S, float4 zt, float B2hi, float B2lo, int& j0, float& fr,
-                                              float& x0) {
+                                              float& rx) {
   // s = S + az (two-sum of the high parts, low parts added)
   float s_hi = __fadd_rn(S.x, zt.x);
   float bb = __fsub_rn(s_hi, S.x);
@@ -599,12 +599,16 @@ __device__ __forceinline__ void node_position(float2 S, float4 zt, float B2hi, f
   e = fmaf(B2lo, s_hi, e);
   float y_hi = __fadd_rn(p, e);
   float y_lo = __fsub_rn(e, __fsub_rn(y_hi, p));
-  // x = sqrt(y): FP32 root plus one Newton correction from the exact residual
-  x0 = __fsqrt_rn(y_hi);
+  // x = sqrt(y): an FP32 root from the reciprocal square root (a few ulp)
+  // plus one Newton correction from the exact residual, which leaves about
+  // 44 bits; rx = 1/x to FP32 accuracy is the caller's (x = 0 only for the
+  // zero-frequency node, where rx = 0)
+  rx = y_hi > 0.0f ? rsqrtf(y_hi) : 0.0f;
+  const float x0 = y_hi * rx;
   float q = __fmul_rn(x0, x0);
   float qe = fmaf(x0, x0, -q);
   float r = __fadd_rn(__fsub_rn(__fsub_rn(y_hi, q), qe), y_lo);
-  float delta = x0 > 0.0f ? r * (0.5f / x0) : 0.0f;  // x = 0 only for the zero-frequency node
+  float delta = 0.5f * r * rx;
   float fl = floorf(x0);
   j0 = (int)fl;
   fr = __fadd_rn(__fsub_rn(x0, fl), delta);
@@ -828,9 +832,9 @@ __device__ __forceinline__ void gather_row(const RowProblem& P, const WindowPoly
     const float4 zt = zt_next;
     if (i + P.tpr < nzh) zt_next = __ldg(&P.zt[lp + P.tpr]);
     int j0;
-    float fr, x0;
-    node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, x0);
-    const float wt = P.wscale * zt.z / x0;
+    float fr, rx;
+    node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, rx);
+    const float wt = P.wscale * zt.z * rx;
     if (lp == nzh || rg.mirror) {
       float2 v, u;
       node_value_pair<H>(P, X, W, j0, fr, v, u);
@@ -867,9 +871,9 @@ __device__ __forceinline__ void gather_row_z(const RowProblem& P, const WindowPo
     const float4 zt = zt_next;
     if (i + P.tpr < nzh) zt_next = __ldg(&P.zt[lp + P.tpr]);
     int j0;
-    float fr, x0;
-    node_position(S, zt, P.B2hi, P.B2lo, j0, fr, x0);
-    const float wt = P.wscale * zt.z / x0;
+    float fr, rx;
+    node_position(S, zt, P.B2hi, P.B2lo, j0, fr, rx);
+    const float wt = P.wscale * zt.z * rx;
     float2 v, u;
     node_value_pair<H>(P, X, W, j0, fr, v, u);
     if (lp == nzh) {
@@ -991,8 +995,8 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
       for (int j = lane; j <= nzh; j += tpr) {
         const float4 zt = __ldg(&P.zt[j]);
         int j0;
-        float fr, x0;
-        node_position(S, zt, P.B2hi, P.B2lo, j0, fr, x0);
+        float fr, rx;
+        node_position(S, zt, P.B2hi, P.B2lo, j0, fr, rx);
         float2 y = Zs[j];
         if (j > 0 && j < nzh) y = cadd(y, Zs[P.nz - j]);
         const float2 pb = make_float2(P.wscale * y.x, P.wscale * y.y);
@@ -1018,9 +1022,9 @@ __device__ __forceinline__ bool adjoint_pairs(const RowProblem& P, const WindowP
         const int lp = i + 1;
         const float4 zt = __ldg(&P.zt[lp]);
         int j0;
-        float fr, x0;
-        node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, x0);
-        const float wt = P.wscale * zt.z / x0;
+        float fr, rx;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0, fr, rx);
+        const float wt = P.wscale * zt.z * rx;
         const float2 ph = node_phase(j0, fr, nt, M, P.nt_over_M);
         const float2 phc = make_float2(ph.x, -ph.y);
         float2 qp, qn;
@@ -1206,8 +1210,8 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
       for (int j = lane; j <= nzh; j += tpr) {
         const float4 zt = __ldg(&P.zt[j]);
         int j0p, j0;
-        float frp, fr, x0;
-        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
+        float frp, fr, rx;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, rx);
         negate_node(j0p, frp, j0, fr);
         float2 y = Zs[j];
         if (j > 0 && j < nzh) {
@@ -1233,9 +1237,9 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
         node_task(i, nzh, nA, lp, neg, nyq);
         const float4 zt = __ldg(&P.zt[lp]);
         int j0p, j0;
-        float frp, fr, x0;
-        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
-        const float wt = P.wscale * zt.z / x0;
+        float frp, fr, rx;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, rx);
+        const float wt = P.wscale * zt.z * rx;
         negate_node(j0p, frp, j0, fr);
         if (nyq) {
           const float2 y = Zs[nzh];
@@ -1269,9 +1273,9 @@ __global__ void __launch_bounds__(1024) row_adjoint_kernel(RowLaunch L, WindowPo
         node_task(i, nzh, nA, lp, neg, nyq);
         const float4 zt = __ldg(&P.zt[lp]);
         int j0p, j0;
-        float frp, fr, x0;
-        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, x0);
-        const float wt = P.wscale * zt.z / x0;
+        float frp, fr, rx;
+        node_position(rg.S, zt, P.B2hi, P.B2lo, j0p, frp, rx);
+        const float wt = P.wscale * zt.z * rx;
         negate_node(j0p, frp, j0, fr);
         if (nyq) {
           float2 y = in1[lp];
