@@ -148,6 +148,55 @@ def oracle_rate(geoms, datas, target_s: float = 10.0):
 # clocks
 # ---------------------------------------------------------------------------
 
+class NvmlClocks:
+    """In-process SM clock, power and clock-event-reason samples through NVML
+    (read-only queries of the driver library, every 2 ms), so that a timed region
+    of a few milliseconds still holds samples."""
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, uuid):
+        import ctypes
+        self.ct = ctypes
+        self.samples = []
+        self.stop_flag = threading.Event()
+        self.thread = None
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle for " + uuid)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _read(self):
+        ct = self.ct
+        clk, mx, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            t = time.time()
+            ok = (self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0 and
+                  self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0 and
+                  self.reasons_fn(self.h, ct.byref(rs)) == 0)
+            pw = float(mw.value) / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw)) == 0 else None
+            if ok:
+                self.samples.append((t, float(clk.value), float(mx.value), pw, int(rs.value)))
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        if self.thread:
+            self.thread.join(timeout=5)
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -158,6 +207,7 @@ class ClockSampler:
         self.proc = None
         self.thread = None
         self.dev = device_index
+        self.nvml = None
 
     def start(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
@@ -168,7 +218,13 @@ class ClockSampler:
         except Exception:
             pass
         if uuid:
-            cmd += ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            cmd += ["-i", uuid]
+            try:
+                self.nvml = NvmlClocks(uuid)
+                self.nvml.start()
+            except Exception:
+                self.nvml = None
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
@@ -182,6 +238,8 @@ class ClockSampler:
             self.samples.append((time.time(), line.strip()))
 
     def stop(self):
+        if self.nvml:
+            self.nvml.stop()
         if self.proc:
             self.proc.terminate()
             try:
@@ -192,6 +250,14 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self, t0: float, t1: float):
+        if self.nvml:
+            inside = [r for r in self.nvml.samples if t0 <= r[0] <= t1]
+            if inside:
+                pw = [r[3] for r in inside if r[3] is not None]
+                reasons = sorted({name for r in inside for bit, name in NvmlClocks.REASONS.items() if r[4] & bit})
+                return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                        "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(inside),
+                        "window": "timed region", "source": "NVML, every 2 ms"}
         rows = []
         for ts, line in self.samples:
             parts = [x.strip() for x in line.split(",")]

@@ -268,7 +268,9 @@ __device__ __forceinline__ void tw_apply(float2 (&v)[R], const TwBase<R>& t) {
 // PADI(a + 16 r) = PADI(a) + 16 r + r/2 (r < 16).  Both hold for every pass
 // after the first radix-16 one (Ns = 16 or a multiple of 256), and for the
 // first pass (Ns = 1) PADI(16 j + r) = PADI(16 j) + r.
-template <int R, bool INV, int OUT>
+// CHAIN_R: the smallest radix whose last pass derives its twiddles by
+// rotation (tw_shift); below it they come from the table.
+template <int R, bool INV, int OUT, int CHAIN_R = 2>
 __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int tpr, const float2* __restrict__ tw,
                                          int twstride, bool active = true) {
   constexpr int NB = kElemsPerThread / R;
@@ -279,7 +281,7 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
   // A last pass of radix < 16 (several butterflies per thread, at j = lane +
   // i M/16): their twiddles follow from the first butterfly's by constant
   // rotations (tw_shift) instead of table loads.
-  const bool chain = NB > 1 && Ns > 1 && Ns * R == M && tpr * kElemsPerThread == M;
+  const bool chain = R >= CHAIN_R && NB > 1 && Ns > 1 && Ns * R == M && tpr * kElemsPerThread == M;
   // twiddles do not depend on the data: for radix 16 (one butterfly per
   // thread) their loads are issued before the barrier; smaller radices carry
   // several butterflies per thread and load after it to stay within registers
@@ -465,7 +467,7 @@ __device__ __forceinline__ bool first_pass32(int M, int mshift, int nt) {
 
 // Remaining passes after a first pass of radix 2^ns_shift (16 or 32: Ns on
 // entry); the last pass writes layout OUT.
-template <bool INV, int OUT>
+template <bool INV, int OUT, int CHAIN_R = 2>
 __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane, int tpr, const float2* tw,
                                          int twstride, bool active = true, int ns_shift = 4) {
   int Ns = 1 << ns_shift;
@@ -479,9 +481,9 @@ __device__ __forceinline__ void fft_rest(float2* X, int M, int mshift, int lane,
     Ns <<= 4;
     rem -= 4;
   }
-  if (rem == 3) fft_pass<8, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
-  else if (rem == 2) fft_pass<4, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
-  else if (rem == 1) fft_pass<2, INV, OUT>(X, M, Ns, lane, tpr, tw, twstride, active);
+  if (rem == 3) fft_pass<8, INV, OUT, CHAIN_R>(X, M, Ns, lane, tpr, tw, twstride, active);
+  else if (rem == 2) fft_pass<4, INV, OUT, CHAIN_R>(X, M, Ns, lane, tpr, tw, twstride, active);
+  else if (rem == 1) fft_pass<2, INV, OUT, CHAIN_R>(X, M, Ns, lane, tpr, tw, twstride, active);
 }
 
 // Inverse length-M transform of an adjoint row with the crop fused: the
@@ -916,7 +918,9 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     const bool r32 = first_pass32(M, P.mshift, P.nt);
     if (r32) fft_first_pass32_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
     else fft_first_pass_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
-    fft_rest<false, kLayoutFlatGhost>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift, true, r32 ? 5 : 4);
+    // (rotated twiddles only in radix-8 last passes: the register pressure of
+    // the radix-2/4 ones costs this kernel more than the table loads)
+    fft_rest<false, kLayoutFlatGhost, 8>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift, true, r32 ? 5 : 4);
     if (valid) {
       if (!ZF) gather_row<H>(P, W, X, row, lane);
       else gather_row_z<H>(P, W, X, P.fh + (size_t)row * P.nz, row, lane);
