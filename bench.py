@@ -314,9 +314,14 @@ def hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the row kernels' source with // comments and blank lines removed
+    (a comment edit leaves the recorded traffic valid; any code edit voids it)."""
+    import re
     h = hashlib.sha256()
     for f in ("pai_row_kernels.cuh",):
-        h.update(open(os.path.join(ROOT, "paper_0808_3510_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_0808_3510_gb300", "csrc", f), encoding="utf-8").read()
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

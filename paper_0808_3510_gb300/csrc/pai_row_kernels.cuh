@@ -9,7 +9,9 @@
 //      oversampled length M = c nt, written straight into shared memory;
 //   2. the length-M FFT of Eq. (nufft-c), in shared memory (Stockham
 //      autosort, radix 16/8/4/2, each thread holding 16 values in registers
-//      per pass);
+//      per pass; at oversampling 2 the first pass skips the zero padding, as
+//      two length-8 DFTs or, for M = 32 16^k, as a radix-32 pass shared by
+//      two threads);
 //   3. the truncated window gather of Eq. (nufft-a) at the nodes
 //      omega = c_s sign(Kz) |K| (Eq. dft-2d), multiplied by the weight of
 //      Eq. (fft-0), written to the half image spectrum.
