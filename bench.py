@@ -105,12 +105,18 @@ def voxels_of(geoms) -> int:
 # oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(geoms, datas, target_s: float = 10.0):
+# wall-clock budget of a whole `--impl reference` run (the oracle on the host cores)
+REF_BUDGET_S = 150.0
+
+
+def oracle_rate(geoms, datas, target_s: float = 10.0, per_row_hint: float = 0.0):
     """Voxels/s of the FP64 oracle, estimated from a bounded sample: direct
     lateral DFT rows plus direct NUDFT rows (steps 1-3 of the direct Fourier
     reconstruction) for a subset of lateral frequencies of the first problem,
     extrapolated to all rows of every problem.  The final inverse DFT is not
-    timed, so the rate is an upper bound on the oracle's speed."""
+    timed, so the rate is an upper bound on the oracle's speed.  per_row_hint:
+    wall seconds per row measured earlier (skips the calibration run); at
+    least one row per thread is timed."""
     import oracle
     import phantoms as ph
 
@@ -128,8 +134,7 @@ def oracle_rate(geoms, datas, target_s: float = 10.0):
         return time.perf_counter() - t
 
     n = max(1, oracle.threads())
-    t = run(n)
-    per_row = t / n
+    per_row = per_row_hint if per_row_hint > 0 else run(n) / n
     rows = int(min(nrows_total, max(n, target_s / max(per_row, 1e-9))))
     t = run(rows)
     per_row = t / rows
@@ -141,7 +146,7 @@ def oracle_rate(geoms, datas, target_s: float = 10.0):
     sample = (f"{rows} of {nrows_total} lateral-frequency rows of problem 0 (direct lateral DFT row + direct "
               f"NUDFT at {G.nz} nodes, FP64), {t:.1f} s wall on {n} threads, extrapolated by operation count "
               f"to the whole workload; inverse DFT not timed (rate is an upper bound)")
-    return voxels_of(geoms) / est, n, sample, t
+    return voxels_of(geoms) / est, n, sample, per_row
 
 
 # ---------------------------------------------------------------------------
@@ -665,8 +670,8 @@ def run_cutoff(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000; 20 for --impl reference)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 20; 3 for --impl reference)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="large2d", choices=["large2d", "plain2d", "planar3d", "adjoint3d",
                                                             "batched2d", "frames2d", "forward3d", "forward2d",
@@ -676,6 +681,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-problem batched-vs-plain measurement of the default run")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 2000
+    if args.warmup is None:
+        args.warmup = 3 if args.impl == "reference" else 20
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -693,8 +702,12 @@ def main():
         desc, geoms, datas = workload(args.config)
         vals = []
         cores, sample = 0, ""
+        # each step a bounded sample: about REF_BUDGET_S seconds for the whole
+        # run, at most 2 s and at least one row per thread per step
+        target = min(2.0, REF_BUDGET_S / (args.warmup + args.steps))
+        per_row = 0.0
         for i in range(args.warmup + args.steps):
-            v, cores, sample, _ = oracle_rate(geoms, datas, target_s=2.0)
+            v, cores, sample, per_row = oracle_rate(geoms, datas, target_s=target, per_row_hint=per_row)
             if i >= args.warmup:
                 vals.append(v)
         value = float(statistics.median(vals))
