@@ -272,12 +272,17 @@ class ClockSampler:
     def summary(self, t0: float, t1: float):
         if self.nvml:
             inside = [r for r in self.nvml.samples if t0 <= r[0] <= t1]
+            window = "timed region"
+            if not inside:
+                # a region shorter than the 10 ms period: the samples next to it
+                inside = [r for r in self.nvml.samples if t0 - 0.015 <= r[0] <= t1 + 0.015]
+                window = "timed region +- 15 ms"
             if inside:
                 pw = [r[3] for r in inside if r[3] is not None]
                 reasons = sorted({name for r in inside for bit, name in NvmlClocks.REASONS.items() if r[4] & bit})
                 return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
                         "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(inside),
-                        "window": "timed region", "source": "NVML, every 10 ms, separate process"}
+                        "window": window, "source": "NVML, every 10 ms, separate process"}
         rows = []
         for ts, line in self.samples:
             parts = [x.strip() for x in line.split(",")]
