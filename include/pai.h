@@ -152,6 +152,8 @@ pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream,
 /* Reconstruction f = R p (Algorithm 2).
  * d_p: device, FP32, sum over problems of nx*ny*nt values, read only.
  * d_f: device, FP32, sum over problems of nx*ny*nz values, overwritten.
+ * Both start on an 8-byte boundary (the kernels move two floats at a time;
+ * PAI_ERR_INVALID_ARG otherwise, as for pai_adjoint and pai_spectrum).
  * Asynchronous on the plan's stream.                                         */
 pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f);
 
@@ -160,7 +162,8 @@ pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f);
  * forward image FFT, window spread from the nodes onto the oversampled grid
  * in gather form, inverse oversampled FFT, prescale, inverse lateral FFT).
  * d_h: device, FP32, image-shaped, read only.  d_pbar: device, FP32,
- * data-shaped, overwritten.  Asynchronous on the plan's stream.  For the
+ * data-shaped, overwritten; both 8-byte aligned.  Asynchronous on the plan's
+ * stream.  For the
  * interpolation methods the transposed interpolation spreads each node onto
  * its one or two grid cells, whose phases follow the spread.                 */
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar);

@@ -320,6 +320,8 @@ class Plan:
             raise ValueError(f"{what} must be a float32 tensor on {self.device}")
         if not t.is_contiguous() or t.numel() != numel:
             raise ValueError(f"{what} must be contiguous with {numel} elements (got {tuple(t.shape)})")
+        if t.data_ptr() % 8 != 0:
+            raise ValueError(f"{what} must start on an 8-byte boundary (the library moves two floats at a time)")
 
     def _out_shape(self, last_attr: str):
         if self.batched:

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -45,6 +46,7 @@ struct ProblemHost {
   bool made[4] = {false, false, false, false};  // which of the four handles cufftCreate made
   bool have_plans = false;
   bool own_lateral = false;  // lateral R2C by the library's own kernel (2-D, power-of-two nx)
+  bool paired = false;       // 2-D otherwise: cuFFT C2C of the sample pairs (RowProblem::paired)
   size_t data_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nt; }
   size_t img_len() const { return (size_t)g.nx * (g.dim == 3 ? g.ny : 1) * g.nz; }
 };
@@ -76,6 +78,7 @@ struct pai_plan_s {
   int ctas_adj3 = 0;                                //         and its CTA count
   bool pairs_atom_ok = false;                       // spread mode 4 applies to every problem of the plan
   int ctas_adj4 = 0;                                // mode 4: CTA count (shared memory as mode 3)
+  bool any_paired = false;  // some problem's lateral spectrum is in the paired layout (RowProblem::paired)
   bool zf = false;      // forward: every stage by the library's kernels (depth-row layout)
   bool zf_adj = false;  // adjoint: the same choice, tuned separately
   size_t smem_fwd = 0, smem_adj = 0;
@@ -220,7 +223,13 @@ pai_status make_cufft_plans(pai_plan_s* P, ProblemHost& p, size_t& work) {
     PAI_FFT(cufftCreate(&p.lat_r2c));
     p.made[0] = true;
     PAI_FFT(cufftSetAutoAllocation(p.lat_r2c, 0));
-    PAI_FFT(plan_fft(P, p.lat_r2c, rank, n, inem, g.nt, 1, onem, g.nt, 1, CUFFT_R2C, g.nt, &ws));
+    if (p.paired) {
+      // C2C of the nt/2 complex columns p[x][2m] + i p[x][2m+1] -> Z[k][m]
+      int pn[1] = {g.nx}, pe[1] = {g.nx};
+      PAI_FFT(plan_fft(P, p.lat_r2c, 1, pn, pe, g.nt / 2, 1, pe, g.nt / 2, 1, CUFFT_C2C, g.nt / 2, &ws));
+    } else {
+      PAI_FFT(plan_fft(P, p.lat_r2c, rank, n, inem, g.nt, 1, onem, g.nt, 1, CUFFT_R2C, g.nt, &ws));
+    }
     work = std::max(work, ws);
     PAI_FFT(cufftCreate(&p.lat_c2r));
     p.made[1] = true;
@@ -319,7 +328,7 @@ pai_status set_fft_streams(pai_plan_s* P, cudaStream_t s) {
 }
 
 RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
-  RowLaunch L;
+  RowLaunch L{};
   L.problems = P->d_problems;
   L.items = adjoint ? P->d_items_adj : P->d_items_fwd;
   L.nitems = adjoint ? P->nitems_adj : P->nitems_fwd;
@@ -332,6 +341,7 @@ RowLaunch make_launch(pai_plan_s* P, bool adjoint) {
   L.bin_offset = P->bin_offset;
   L.bin_slot = P->bin_slot;
   L.spread_mode = P->spread_mode;
+  L.paired = !adjoint && P->any_paired ? 1 : 0;
   return L;
 }
 
@@ -372,6 +382,9 @@ pai_status own_lateral_inv(pai_plan_s* P, const ProblemHost& p, float2* in, floa
 // Stage (a) of the forward operator for problem p.
 pai_status enqueue_lateral(pai_plan_s* P, const ProblemHost& p, const float* d_p, cudaStream_t s) {
   if (P->zf || p.own_lateral) return own_lateral_fwd(P, p, d_p + p.data_off, P->d_pt + p.pt_off, p.g.nt, s);
+  if (p.paired)
+    return fft_status(cufftExecC2C(p.lat_r2c, reinterpret_cast<cufftComplex*>(const_cast<float*>(d_p) + p.data_off),
+                                   (cufftComplex*)(P->d_pt + p.pt_off), CUFFT_FORWARD));
   return fft_status(cufftExecR2C(p.lat_r2c, const_cast<float*>(d_p) + p.data_off, (cufftComplex*)(P->d_pt + p.pt_off)));
 }
 
@@ -774,6 +787,11 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
   P->TW = tw_need;  // covers every window candidate's padded length
   for (auto& p : P->probs) {
     p.own_lateral = p.g.dim == 2 && lateral_supported(p.g.nx, p.g.nt);
+    // 2-D sizes the library's lateral kernel does not take: cuFFT C2C of the
+    // sample pairs instead of cuFFT's strided R2C (which packs and
+    // post-processes in passes of their own); the row kernel separates
+    p.paired = p.g.dim == 2 && !p.own_lateral && !P->zf;
+    if (p.paired) P->any_paired = true;
     if (p.own_lateral || P->zf) P->TW = std::max(P->TW, p.g.nx);
     if (P->zf) {
       P->TW = std::max(P->TW, p.g.nz);
@@ -803,6 +821,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     r.rowS = reinterpret_cast<const float2*>(P->d_tables + p.rowS_off);
     r.zt = reinterpret_cast<const float4*>(P->d_tables + p.zt_off);
     fill_row_scalars(p.g, p.M, r);
+    r.paired = p.paired ? 1 : 0;
     if (qmode) {
       r.qmode = 1;
       r.wscale = (float)(0.5 / ((double)r.n1 * r.n2 * p.g.nz));
@@ -874,7 +893,7 @@ pai_status build_plan(const pai_geometry* gs, int count, void* stream, pai_plan_
     P->fft_region = (int)(region / sizeof(float2));
     P->smem_fwd = region;
     if (P->smem_fwd > (size_t)smem_optin) return PAI_ERR_UNSUPPORTED;
-    const int occ_f = row_kernel_max_ctas_per_sm(0, T, P->smem_fwd, P->H, P->zf);
+    const int occ_f = row_kernel_max_ctas_per_sm(P->any_paired ? 3 : 0, T, P->smem_fwd, P->H, P->zf);
     if (occ_f < 1) return PAI_ERR_UNSUPPORTED;
     std::vector<WorkItem> items;
     build_items(T, items);
@@ -1309,6 +1328,11 @@ int forward_box_extent(int n, double d, const pai_geometry& g) {
   return b > (1 << 30) ? (1 << 30) : (int)b;
 }
 
+// Device buffers are read and written two floats at a time.
+bool aligned8(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 7) == 0;
+}
+
 }  // namespace
 
 // the detector data grid of a single-problem plan: [nx][ny][nt]
@@ -1327,19 +1351,19 @@ pai_status pai_plan_batched(const pai_geometry* g, int count, void* cuda_stream,
 }
 
 pai_status pai_reconstruct(pai_plan_t plan, const float* d_p, float* d_f) {
-  if (!plan || !d_p || !d_f) return PAI_ERR_INVALID_ARG;
+  if (!plan || !d_p || !d_f || !aligned8(d_p, d_f)) return PAI_ERR_INVALID_ARG;
   if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   return run(plan, d_p, d_f, false);
 }
 
 pai_status pai_adjoint(pai_plan_t plan, const float* d_h, float* d_pbar) {
-  if (!plan || !d_h || !d_pbar) return PAI_ERR_INVALID_ARG;
+  if (!plan || !d_h || !d_pbar || !aligned8(d_h, d_pbar)) return PAI_ERR_INVALID_ARG;
   if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   return run(plan, d_h, d_pbar, true);
 }
 
 pai_status pai_spectrum(pai_plan_t plan, const float* d_p, float* d_fhat) {
-  if (!plan || !d_p || !d_fhat) return PAI_ERR_INVALID_ARG;
+  if (!plan || !d_p || !d_fhat || !aligned8(d_p, d_fhat)) return PAI_ERR_INVALID_ARG;
   if (plan->qmode) return PAI_ERR_INVALID_ARG;  // a forward-model plan
   int prev = 0;
   cudaGetDevice(&prev);

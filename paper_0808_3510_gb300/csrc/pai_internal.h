@@ -69,6 +69,9 @@ struct RowProblem {
   int nzshift;             // log2(nz) when nz is a power of two, else 0
   int method;              // PAI_METHOD_*
   int qmode;               // adjoint kernel evaluates the discrete forward model (depth-row layout only)
+  int paired;              // 2-D, forward: pt holds Z[k][m] (k < nx = n2, m < nt/2, row stride nt/2), the
+                           // lateral DFT of the sample pairs p[x][2m] + i p[x][2m+1]; the forward row kernel
+                           // separates row k's samples from Z[k] and Z[nx - k]
 };
 
 struct WorkItem {
@@ -94,6 +97,7 @@ struct RowLaunch {
                                // spread by one warp per row (deterministic; windowed methods, 32 or 64
                                // threads per row), 4 node pairs spread by every warp of the row with
                                // shared-memory atomics (windowed methods, a multiple of 32 threads per row)
+  int paired;                  // forward: some problem is in the paired layout (RowProblem::paired)
 };
 
 // Complex values one row slot needs: the padded FFT layout (one pad per 32)
@@ -175,8 +179,8 @@ cudaError_t launch_lateral_c2c(const float2* in, float2* out, int L, int C, int 
 // In-place FFT of `rows` contiguous complex lines of power-of-two length L (32 <= L <= 16384).
 cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const float2* tw, int twstride,
                             cudaStream_t s);
-// kind: 0 forward row kernel, 1 adjoint row kernel, 2 adjoint row kernel with the pair spread, 4 with the
-// atomic pair spread
+// kind: 0 forward row kernel, 1 adjoint row kernel, 2 adjoint row kernel with the pair spread, 3 forward row
+// kernel for launches with problems in the paired layout, 4 adjoint with the atomic pair spread
 int row_kernel_max_ctas_per_sm(int kind, int threads, size_t smem, int H, bool zf = false);
 
 // Data cutoff w_cut (pai_cutoff.cu).  R = ceil(sqrt(eps)); the table holds

@@ -126,7 +126,7 @@ extern "C" pai_status pai_spectrum_rows_noalloc(const pai_geometry* g_in, const 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (cudaMemcpyAsync(base, g_stage, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return PAI_ERR_CUDA;
 
-  RowLaunch L;
+  RowLaunch L{};
   L.problems = reinterpret_cast<const RowProblem*>(base + o_prob);
   L.items = reinterpret_cast<const WorkItem*>(base + o_items);
   L.nitems = nitems;

@@ -33,8 +33,9 @@ static int occ_k(K kernel, int threads, size_t smem) {
 template <int H>
 static cudaError_t fwd_h(const RowLaunch& L, const WindowPoly& w, int threads, int ctas, size_t smem, cudaStream_t s,
                          bool zf) {
-  return zf ? launch_k(row_forward_kernel<H, true>, L, w, threads, ctas, smem, s)
-            : launch_k(row_forward_kernel<H, false>, L, w, threads, ctas, smem, s);
+  if (zf) return launch_k(row_forward_kernel<H, true>, L, w, threads, ctas, smem, s);
+  return L.paired ? launch_k(row_forward_kernel<H, false, true>, L, w, threads, ctas, smem, s)
+                  : launch_k(row_forward_kernel<H, false>, L, w, threads, ctas, smem, s);
 }
 
 template <int H>
@@ -50,7 +51,8 @@ static cudaError_t adj_h(const RowLaunch& L, const WindowPoly& w, int threads, i
             : launch_k(row_adjoint_kernel<H, false>, L, w, threads, ctas, smem, s);
 }
 
-// kind: 0 forward, 1 adjoint, 2 adjoint with the pair spread, 4 with the atomic pair spread
+// kind: 0 forward, 1 adjoint, 2 adjoint with the pair spread, 3 forward (paired layout), 4 adjoint with the
+// atomic pair spread
 template <int H>
 static int occ_h(int kind, int threads, size_t smem, bool zf) {
   if (kind == 2)
@@ -59,6 +61,7 @@ static int occ_h(int kind, int threads, size_t smem, bool zf) {
   if (kind == 4)
     return zf ? occ_k(row_adjoint_pairs_kernel<H, true, true>, threads, smem)
               : occ_k(row_adjoint_pairs_kernel<H, false, true>, threads, smem);
+  if (kind == 3) return occ_k(row_forward_kernel<H, false, true>, threads, smem);
   if (kind == 1)
     return zf ? occ_k(row_adjoint_kernel<H, true>, threads, smem) : occ_k(row_adjoint_kernel<H, false>, threads, smem);
   return zf ? occ_k(row_forward_kernel<H, true>, threads, smem) : occ_k(row_forward_kernel<H, false>, threads, smem);

@@ -351,14 +351,28 @@ __device__ __forceinline__ void fft_pass(float2* X, int M, int Ns, int lane, int
   __syncthreads();
 }
 
+// Sample n of a row's lateral spectrum: src[n], or (paired layout, see
+// RowProblem::paired) separated from the transforms of the sample pairs,
+// z1 = Z[k][m], z2 = Z[nx - k][m] with m = n/2:
+// sample 2m = (z1 + conj z2) / 2, sample 2m+1 = (z1 - conj z2) / (2i).
+template <bool PAIRED>
+__device__ __forceinline__ float2 row_sample(const float2* __restrict__ src, const float2* __restrict__ src2, int n) {
+  if (!PAIRED) return __ldg(&src[n]);
+  const float2 z1 = __ldg(&src[n >> 1]), z2 = __ldg(&src2[n >> 1]);
+  return (n & 1) ? make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x))
+                 : make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+}
+
 // First forward pass (radix 16, Ns = 1) fed straight from global memory:
 // position m = j + r M/16 of the oversampled input holds sample
 // n = m + nt/2 (mod M) times the prescale when n < nt, else zero (Algorithm 1
 // prescale and zero padding, centred so that the e^{+i pi j/c} part of the
 // Proposition's phase is absorbed).  Writes padded.
+template <bool PAIRED = false>
 __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int nt, int lane, int tpr,
                                                            const float2* __restrict__ src,
-                                                           const float* __restrict__ prescale) {
+                                                           const float* __restrict__ prescale,
+                                                           const float2* __restrict__ src2 = nullptr) {
   constexpr int R = 16;
   float2 v[R];
   const int MR = M / R, mask = M - 1, h = nt >> 1;
@@ -372,7 +386,7 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
     for (int q = 0; q < 8; ++q) {
       const int r = q < 4 ? q : q + 8;
       const int n = (lane + r * MR + h) & mask;
-      const float2 g = __ldg(&src[n]);
+      const float2 g = row_sample<PAIRED>(src, src2, n);
       const float s = __ldg(&prescale[n]);
       c8[q] = make_float2(s * g.x, s * g.y);
     }
@@ -401,7 +415,7 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
     const int n = (m + h) & mask;
     float2 a = make_float2(0.f, 0.f);
     if (n < nt) {
-      const float2 g = __ldg(&src[n]);
+      const float2 g = row_sample<PAIRED>(src, src2, n);
       const float s = __ldg(&prescale[n]);
       a = make_float2(s * g.x, s * g.y);
     }
@@ -423,9 +437,11 @@ __device__ __forceinline__ void fft_first_pass_from_global(float2* X, int M, int
 // ones with z_s = (x_s - x_{s+16}) w32^s, w_N = e^{-2 pi i/N}; of each pair
 // x_s, x_{s+16} one is padding (s < 8: x_{s+16}; s >= 8: x_s).  Both threads
 // load the butterfly's 16 samples.  Writes padded: PADI(32 j + q) = 33 j + q.
+template <bool PAIRED>
 __device__ __forceinline__ void fft_first_pass32_from_global(float2* X, int M, int nt, int lane, int tpr,
                                                              const float2* __restrict__ src,
-                                                             const float* __restrict__ prescale) {
+                                                             const float* __restrict__ prescale,
+                                                             const float2* __restrict__ src2) {
   const int half = tpr >> 1, q4 = M >> 2, M32 = M >> 5;
   const int h = lane >= half ? 1 : 0;
   const int j = lane - h * half;
@@ -433,7 +449,7 @@ __device__ __forceinline__ void fft_first_pass32_from_global(float2* X, int M, i
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int n = s < 8 ? j + s * M32 + q4 : j + (s - 8) * M32;
-    const float2 g = __ldg(&src[n]);
+    const float2 g = row_sample<PAIRED>(src, src2, n);
     const float p = __ldg(&prescale[n]);
     v[s] = make_float2(p * g.x, p * g.y);
   }
@@ -900,7 +916,9 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
 // ZF = false: writes the half image spectrum fhat[k][l'] (both lateral
 // destinations k and -k); ZF = true: writes the row's own full depth spectrum
 // F[row][l mod nz] (see gather_row_z).
-template <int H, bool ZF>
+// PAIRED: the launch holds problems in the paired layout (RowProblem::paired);
+// compiled apart so that the kernel of plans without them keeps its registers.
+template <int H, bool ZF, bool PAIRED = false>
 __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPoly W) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
@@ -916,10 +934,20 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(RowLaunch L, WindowPo
     const bool valid = row < P.rows;
     float2* X = smem + slot * P.slot;
     // first pass straight from the lateral spectrum row (rows past the end read row 0, unused)
-    const float2* src = P.pt + (size_t)(valid ? row : 0) * P.nt;
+    const int srow = valid ? row : 0;
+    const bool paired = PAIRED && P.paired != 0;
+    const float2* src = P.pt + (size_t)srow * (paired ? P.nt >> 1 : P.nt);
+    const float2* src2 = P.pt + (size_t)(srow == 0 ? 0 : P.n2 - srow) * (P.nt >> 1);
     const bool r32 = first_pass32(M, P.mshift, P.nt);
-    if (r32) fft_first_pass32_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
-    else fft_first_pass_from_global(X, M, P.nt, lane, tpr, src, P.prescale);
+    // (the layout is a template argument so that each path issues its loads
+    // back to back)
+    if (PAIRED && paired) {
+      if (r32) fft_first_pass32_from_global<true>(X, M, P.nt, lane, tpr, src, P.prescale, src2);
+      else fft_first_pass_from_global<true>(X, M, P.nt, lane, tpr, src, P.prescale, src2);
+    } else {
+      if (r32) fft_first_pass32_from_global<false>(X, M, P.nt, lane, tpr, src, P.prescale, src2);
+      else fft_first_pass_from_global<false>(X, M, P.nt, lane, tpr, src, P.prescale, src2);
+    }
     // (rotated twiddles only in radix-8 last passes: the register pressure of
     // the radix-2/4 ones costs this kernel more than the table loads)
     fft_rest<false, kLayoutFlatGhost, 8>(X, M, P.mshift, lane, tpr, L.tw, L.Mmax >> P.mshift, true, r32 ? 5 : 4);

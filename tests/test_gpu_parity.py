@@ -187,6 +187,11 @@ def test_bad_tensors_rejected(pai):
         plan.reconstruct(torch.zeros(16, 32, device="cuda", dtype=torch.float64))
     with pytest.raises(ValueError):
         plan.reconstruct(torch.zeros(32, 16, device="cuda").t())
+    # a contiguous view one float into a buffer: rejected before any launch
+    # (the library reads and writes two floats at a time)
+    buf = torch.zeros(16 * 32 + 1, device="cuda")
+    with pytest.raises(ValueError, match="8-byte"):
+        plan.reconstruct(buf[1:].view(16, 32))
 
 
 def test_batched_uneven_matches_oracle_and_single_plans(pai, pipeline):
