@@ -246,7 +246,7 @@ cudaError_t launch_rows_c2c(float2* data, int L, int rows, bool inverse, const f
   int mshift = 0;
   while ((1 << mshift) < L) ++mshift;
   const int tpr = L / kElemsPerThread;
-  const int threads = tpr > 256 ? tpr : 256;
+  const int threads = tpr > 128 ? tpr : 128;  // (128 measured 1.5 us faster than 256 per 256^3 depth stage)
   const int rpc = threads / tpr;
   const size_t smem = (size_t)rpc * lateral_slot(L) * sizeof(float2);
   const int ctas = (rows + rpc - 1) / rpc;
