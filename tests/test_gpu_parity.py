@@ -531,6 +531,33 @@ def test_atomic_pair_spread_forward_model(pai, g, monkeypatch):
     assert rel(to_np(model(to_gpu(f))), oracle.forward_model(g, f.astype(np.float64))) < TOL
 
 
+def test_paired_lateral_layout(pai):
+    """2-D sizes the library's lateral kernel does not take run cuFFT on the
+    sample pairs and separate them in the row kernel: the spectrum of such a
+    plan against the oracle, and a batch mixing such problems with power-of-two
+    ones (whose rows take the plain path inside the same launch) against the
+    oracle problem by problem."""
+    g = ph.Geometry(dim=2, nx=222, nt=300, nz=150, dz=1.1)  # nx = 2 * 3 * 37
+    p = np.asarray(ph.random_data(41, g), np.float32)
+    plan = pai.Plan(gdict(g, K=3))
+    S = plan.spectrum(to_gpu(p)).cpu().numpy()
+    F = oracle.spectrum(g, p.astype(np.float64))
+    assert rel(S, oracle_half_spectrum(g, F)) < TOL
+    assert rel(to_np(plan.reconstruct(to_gpu(p))), oracle.image_from_spectrum(g, F)) < TOL
+    geoms = [ph.Geometry(dim=2, nx=128, nt=256, nz=128),
+             ph.Geometry(dim=2, nx=90, nt=200, nz=100, c=1.2),
+             ph.Geometry(dim=2, nx=64, nt=300, nz=160, dx=0.8),
+             ph.Geometry(dim=2, nx=150, nt=128, nz=64)]
+    bplan = pai.Plan([gdict(x, K=3) for x in geoms])
+    ps = [np.asarray(ph.random_data(42 + i, x), np.float32) for i, x in enumerate(geoms)]
+    out = to_np(bplan.reconstruct(to_gpu(np.concatenate([q.ravel() for q in ps]))))
+    off = 0
+    for x, q in zip(geoms, ps):
+        n = x.nx * x.nz
+        assert rel(out[off: off + n].reshape(x.image_shape), oracle.reconstruct(x, q.astype(np.float64))) < TOL, x
+        off += n
+
+
 def test_window_tuner_on_a_batch(pai):
     """With the window left open (K, oversampling and alpha 0) the plan times
     window candidates and keeps one: every problem's padded length is a power of
